@@ -148,6 +148,8 @@ def random_tt(n_t, n_xi_, n_x, r1, r2, seed=0, decay=None):
     z2 = rng.standard_normal((r1, n_xi_, r2))
     z3 = rng.standard_normal((r2, n_x))
     if decay is not None:
+        if r1 > n_t or r2 > n_x or r2 > r1 * n_xi_:
+            raise ValueError("a prescribed spectrum needs ranks no larger than the mode sizes")
         q1, _ = np.linalg.qr(z1)
         z1 = q1[:, :r1] * (10.0 ** (-decay * np.arange(r1) / max(r1, 1)))[None, :]
         q3, _ = np.linalg.qr(z3.T)

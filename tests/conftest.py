@@ -1,6 +1,11 @@
 import os
 import sys
 
+# The oracle is single-threaded on purpose: multithreaded BLAS oversubscribes
+# small containers and runs tens of times slower there.
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))

@@ -186,3 +186,17 @@ def test_inner_preconditioner_solves_its_matrix(tiny):
     K = (d.bM / d.tau + d.bA[0]).toarray()
     Mfull = np.kron(np.kron(It - d.C.toarray(), np.eye(d.n_xi)), K)
     assert np.abs(Mfull @ y - z.vec()).max() < 1e-10 * np.abs(z.vec()).max()
+
+
+@pytest.mark.parametrize("mean", [False, True])
+def test_grouped_convection_equals_term_by_term_sum(tiny, mean):
+    """conv_apply (blocks shared per diag(w1_a) and per N(w3_b)) is the same tensor
+    as summing the Kronecker terms of eq. (N_kron) one at a time."""
+    from oracle.tt import add
+    d = tiny
+    u, _ = _rand_pair(d, 11)
+    w = TT(*synth.random_tt(d.n_t, d.n_xi, 2 * d.n_nodes, 2, 3, seed=12))
+    grouped = d.conv_apply(w, u, mean=mean)
+    literal = add(*[(1.0, t) for t in d.conv_terms(w, u, mean=mean)])
+    assert grouped.ranks == (2 * u.ranks[0], 3 * u.ranks[1])
+    assert np.abs(grouped.vec() - literal.vec()).max() < 1e-12 * np.abs(literal.vec()).max()
