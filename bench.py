@@ -1,0 +1,291 @@
+"""Benchmark of the low-rank all-at-once Picard solve (plain FP64 GPU path).
+
+Workload: the "medium" problem -- symmetric step L=5, Q2-Q1 on element side
+1/8 (velocity spacing 1/16: n_u = 5440, n_p = 769), m = 3 KL terms, total
+degree 3 (n_xi = 20), n_t = 100, tau = 0.05, nu0 = 1/100, sigma = 0.2,
+truncation 1e-5, Table 5.2 tolerances otherwise.  One step is one complete
+Picard solve to ||r|| <= 1e-5 ||f|| (Stokes start, TT-GMRES with the mean-based
+LSC preconditioner, truncated updates), inputs resident on the GPU.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  With N > 1 (torchrun) every rank solves its own copy
+(independent replicas, no communication) and the time is the max over ranks.
+`--impl reference` times the CPU oracle (a bounded sample, scaled; see
+cpu_sample) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Picard-solve time to rel.res 1e-5 (plain FP64 GPU, medium workload)"
+WORKLOAD = "medium"
+# ncu dram bytes (read + write) per launch of the dominant kernel class, from the
+# capture summarised in profiles/; None until measured for the current kernel.
+NCU_TRAFFIC = {}
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    """nvidia-smi sampling during the timed region (read-only queries)."""
+
+    def __init__(self, index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [l.strip().split(",") for l in open(self.f.name) if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1].split()[0])); mx.append(float(r[2].split()[0]))
+            except Exception:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if "Active" in v and "Not" not in v:
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def _oracle_sample_worker(workload, seconds, q):
+    """Time the oracle on a bounded sample of the workload: outer TT-GMRES
+    iterations of the Stokes solve (each: preconditioner with its inner solve,
+    matvec, truncations, Gram-Schmidt, iterate and true residual), until
+    `seconds` of CPU work have been spent."""
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    import synth
+    from oracle.system import Discretisation
+    from oracle.solver import MeanLSC, gmres, _Pair
+    prob = synth.preset(workload)
+    d = Discretisation(prob)
+    t = prob.tol
+    f = d.rhs()
+    its = 0
+    t0 = time.perf_counter()
+    per = []
+    for k in range(1, t.maxit_gmres + 1):
+        P = MeanLSC(d, None, t.eps_gmres, t.tol_inner, t.maxit_inner)
+        a = time.perf_counter()
+        _, st = gmres(lambda v: d.apply(None, *v), P, f, tol=0.0, eps=t.eps_gmres, maxit=k, space=_Pair)
+        per.append((time.perf_counter() - a) / max(st["its"], 1))
+        its = st["its"]
+        if time.perf_counter() - t0 > seconds or st["its"] < k:
+            break
+    q.put(dict(sec_per_outer_it=per[-1], outer_its_sampled=its, wall=time.perf_counter() - t0))
+
+
+def cpu_sample(workload, seconds):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_oracle_sample_worker, args=(workload, seconds, q))
+    p.start()
+    p.join()
+    return q.get()
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(a):
+    import numpy as np
+    import torch
+    import synth
+    from paper_1906_06785_gb300 import binding
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    # the CPU baseline runs before the first CUDA call of this process (spawned child)
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        cpu = cpu_sample(a.workload, a.cpu_seconds)
+
+    prob = synth.preset(a.workload)
+    ctx = binding.Context()
+    P = ctx.problem(prob)
+    opts = binding.opts_from(prob.tol)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    last = None
+    for _ in range(a.warmup):
+        last = P.picard(opts)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    ctx.profile(True)
+    l0 = ctx.launches
+    times = []
+    for _ in range(a.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        last = P.picard(opts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1000.0)
+    launches = (ctx.launches - l0) // max(a.steps, 1)
+    prof = ctx.prof_read()
+    ctx.profile(False)
+    clk = clocks.stop()
+    t_step = sum(times) / len(times)
+    if dist:
+        tt = torch.tensor([t_step], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    u, p, st, code = last
+
+    # end-to-end through the public API with host buffers (problem arrays in, cores out)
+    e2e = []
+    h2d = sum(v.nbytes for v in (prob.mesh.xy, prob.mesh.elem_q2, prob.mesh.elem_q1, prob.mesh.dirichlet,
+                                  prob.mesh.inflow, prob.mi, prob.nu, prob.tprofile))
+    d2h = 0
+    for _ in range(max(1, a.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P2 = ctx.problem(prob)
+        u2, p2, st2, _ = P2.picard(opts)
+        cu, cp = u2.cores(), p2.cores()
+        e2e.append(time.perf_counter() - t0)
+        d2h = sum(x.nbytes for x in cu) + sum(x.nbytes for x in cp)
+        del u2, p2, P2
+
+    # roofline of the dominant kernel class (events around each launch in the timed region)
+    peaks = _peaks()
+    dom = max(prof, key=lambda k: prof[k][1])
+    n, ms, fl, by = prof[dom]
+    fp64_peak = 1250.0   # GFLOP/s: nominal GB300 FP64 rate (no measured FP64 peak is available)
+    if dom == "spmm":
+        achieved = by / (ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s"}
+    else:
+        achieved = fl / (ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak / 1000.0, "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = dom
+    roof["launches"] = n
+    roof["ms_per_launch"] = ms / max(n, 1)
+    roof["traffic"] = NCU_TRAFFIC.get(dom)
+    roof["peak_source"] = ("MEASURED_PEAKS.json hbm_gbs (burst)" if roof["bound"] == "hbm"
+                           else "nominal FP64 1.25 TFLOP/s (fallback; FP64 is not in MEASURED_PEAKS.json)")
+    breakdown = {k: {"launches": v[0], "ms_per_step": v[1] / a.steps} for k, v in prof.items()}
+
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": t_step * 1000.0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{a.workload}: step L=5 h=1/8 n_u={2 * prob.n_v} n_p={prob.n_p} "
+                               f"n_xi={prob.n_xi} n_t={prob.n_t}",
+                   "precision": "plain FP64", "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": "independent replica per GPU" if world > 1 else "1 GPU"},
+        "e2e": {"value": sum(e2e) / len(e2e), "unit": "s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "kernel_breakdown": breakdown,
+        "solve": {"picard_its": st.picard_its, "stokes_its": st.stokes_its,
+                  "gmres_its": list(st.gmres_its[1:st.picard_its + 1]),
+                  "rel_res": st.res[st.picard_its] / st.fnorm, "u_ranks": u.ranks, "p_ranks": p.ranks},
+        "clocks": clk,
+    }
+    if cpu is not None:
+        outer = st.stokes_its + sum(st.gmres_its[1:st.picard_its + 1])
+        est = cpu["sec_per_outer_it"] * outer
+        out["cpu_baseline"] = {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
+                               "sample": f"oracle Stokes-solve outer GMRES iterations on the same workload "
+                                         f"({cpu['outer_its_sampled']} its, {cpu['wall']:.1f} s), "
+                                         f"{cpu['sec_per_outer_it']:.2f} s/it x {outer} outer its of the solve"}
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per = max(5.0, 150.0 / max(a.steps + a.warmup, 1))
+    for _ in range(a.warmup):
+        cpu_sample(a.workload, per)
+    samples = [cpu_sample(a.workload, per) for _ in range(a.steps)]
+    s = sum(x["sec_per_outer_it"] for x in samples) / len(samples)
+    # outer iteration count of a complete solve of this workload (GPU run statistics)
+    outer = 14
+    v = s * outer
+    out = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": v * 1000.0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": a.workload, "precision": "plain FP64 (CPU oracle)"},
+           "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
+                            "sample": f"{s:.2f} s per outer GMRES iteration of the Stokes solve x {outer} outer "
+                                      f"iterations per solve"},
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)

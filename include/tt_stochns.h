@@ -1,0 +1,225 @@
+/*
+ * tt_stochns.h -- C ABI of the GPU low-rank all-at-once solver for the
+ * stochastic unsteady Navier-Stokes problem (Elman & Su, "A low-rank solver
+ * for the stochastic unsteady Navier-Stokes problem").
+ *
+ * Conventions for every entry point:
+ *   - returns an int status: TT_OK (0) or a negative TT_E* code; never throws;
+ *     tt_last_error(ctx) gives a message for the last failure in that context;
+ *   - all GPU work is enqueued on the context's CUDA stream; entry points that
+ *     return host values (norms, ranks, statistics) synchronise that stream;
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     device memory of the current device; the flag arguments say which;
+ *   - objects returned through out-parameters (tt_t, tt_problem, tt_op) are
+ *     owned by the caller and released with their *_destroy function; the
+ *     library copies every input array it keeps.
+ *
+ * Tensor-train layout (Section 4.1, eq. z_tt): a tensor z in
+ * R^{n_t x n_xi x n_x} is z(i1,i2,i3) = sum z1(i1,a1) z2(a1,i2,a2) z3(a2,i3),
+ * with cores passed and returned as
+ *   z1: n_t x r1, column-major          (element (t,a)   at a*n_t + t)
+ *   z2: r1 x n_xi x r2, r2 fastest      (element (a,s,b) at (a*n_xi + s)*r2 + b)
+ *   z3: r2 x n_x, stored as n_x x r2 row-major (element (b,j) at j*r2 + b)
+ * all in float64.  Velocity trains have n_x = n_u = 2 n_v (x1 components of
+ * the free nodes first, then x2 components); pressure trains n_x = n_p;
+ * full-node velocity fields (convection trains) n_x = 2 n_nodes.
+ */
+#ifndef TT_STOCHNS_H
+#define TT_STOCHNS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    TT_OK = 0,
+    TT_EINVAL = -1,      /* bad argument (shape, null pointer, mismatch) */
+    TT_ENOMEM = -2,      /* device or host allocation failed */
+    TT_ECUDA = -3,       /* a CUDA call failed (message in tt_last_error) */
+    TT_ENOCONV = -4,     /* iteration cap reached; best iterate returned */
+    TT_ERANK = -5,       /* a rank would exceed the configured capacity */
+    TT_ENAN = -6,        /* non-finite value met in a norm */
+    TT_ETIMEOUT = -7     /* a device-side wait ran out of its iteration budget */
+};
+
+typedef struct tt_ctx tt_ctx;
+typedef struct tt_t tt_t;
+typedef struct tt_problem tt_problem;
+typedef struct tt_op tt_op;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on the current CUDA device.  cuda_stream: a cudaStream_t
+ * (NULL = the legacy default stream) on which all work of this context runs. */
+int tt_ctx_create(void* cuda_stream, tt_ctx** out);
+int tt_ctx_destroy(tt_ctx* ctx);
+/* Message of the last failure in this context (static storage, never NULL). */
+const char* tt_last_error(const tt_ctx* ctx);
+/* Number of kernels this context has launched so far. */
+long long tt_ctx_launches(const tt_ctx* ctx);
+
+/* Profiling of kernel classes (0 QR, 1 Jacobi SVD, 2 GEMM, 3 SpMM, 4 banded
+ * solve, 5 banded factorisation, 6 core-1/core-2/concatenation kernels,
+ * 7 element assembly): CUDA events around each launch of a class on the
+ * context stream, with the algorithmic flops and bytes of the launch.
+ * tt_ctx_profile resets the counters and turns timing on (1) or off (0);
+ * tt_ctx_prof_read synchronises the stream and returns the totals since the
+ * last reset: launches, milliseconds, flops, bytes. */
+int tt_ctx_profile(tt_ctx* ctx, int enable);
+int tt_ctx_prof_read(tt_ctx* ctx, int slot, long long* launches, double* ms, double* flops,
+                     double* bytes);
+
+/* ---- tensor trains (Section 4.1) ------------------------------------------ */
+
+/* Copy cores (layout above) into a new device-resident train.
+ * src_on_device: 0 = the three pointers are host memory, 1 = device memory. */
+int tt_create(tt_ctx* ctx, int n_t, int n_xi, int n_x, int r1, int r2,
+              const double* z1, const double* z2, const double* z3,
+              int src_on_device, tt_t** out);
+int tt_destroy(tt_t* t);
+int tt_shape(const tt_t* t, int* n_t, int* n_xi, int* n_x, int* r1, int* r2);
+/* Copy the cores out (buffers sized from tt_shape). */
+int tt_get_cores(tt_ctx* ctx, const tt_t* t, double* z1, double* z2, double* z3,
+                 int dst_on_device);
+
+/* Truncation T_eps (Section 4.1): returns a train with
+ * ||T(z) - z||_F <= eps ||z||_F, delta_j = eps ||z|| / sqrt 2 on both
+ * unfoldings, each rank the smallest r >= 1 whose discarded singular values
+ * have sum of squares <= delta^2.  eps <= 0 keeps every nonzero singular
+ * value.  norm_before = ||z||, norm_after = ||T(z)|| (either may be NULL). */
+int tt_round(tt_ctx* ctx, const tt_t* in, double eps, tt_t** out,
+             double* norm_before, double* norm_after);
+
+/* <vec a, vec b> (Section 4.1) into *out (host). */
+int tt_dot(tt_ctx* ctx, const tt_t* a, const tt_t* b, double* out);
+
+/* alpha a + beta b by concatenating cores (ranks add; no truncation). */
+int tt_axpby(tt_ctx* ctx, double alpha, const tt_t* a, double beta, const tt_t* b,
+             tt_t** out);
+
+/* ---- the discrete problem (Sections 3, 5.1) -------------------------------- */
+
+/* Statement of the discrete all-at-once problem.  All arrays are host memory
+ * and are copied.  Node numbering and element orders follow the mesh
+ * generator: a Q2 element lists nodes a + 3b (a along x1, b along x2,
+ * a,b in {0,1,2}); its Q1 vertices a + 2b (a,b in {0,1}); elements are
+ * squares of side h.  nu holds nodal viscosity fields on the Q1 vertices:
+ * nu[0] the mean nu0, nu[l] = nu0 sigma sqrt(beta_l) a_l (l = 1..m); they are
+ * bilinear on each element.  multi_index lists the gPC multi-indices
+ * (n_xi x m, row-major); index 0 must be the constant polynomial.
+ * tprofile[k] is the inflow time factor at t_{k+1}; inflow[j] is the steady
+ * x1-velocity at Dirichlet node j (0 on walls). */
+typedef struct {
+    int n_nodes, n_elem, n_pnodes;
+    double h;
+    const double* xy;               /* n_nodes x 2 */
+    const long long* elem_q2;       /* n_elem x 9 */
+    const long long* elem_q1;       /* n_elem x 4 */
+    const unsigned char* dirichlet; /* n_nodes, 1 = Dirichlet */
+    const double* inflow;           /* n_nodes */
+    int m, n_xi;
+    const long long* multi_index;   /* n_xi x m */
+    const double* nu;               /* (m + 1) x n_pnodes */
+    int n_t;
+    double tau;
+    const double* tprofile;         /* n_t */
+} tt_problem_desc;
+
+/* Build the device-resident discretisation: Q2-Q1 matrices of eq. (mat_entries)
+ * and B (free and Dirichlet column blocks), the gPC matrices G_l, H_l
+ * (Section 3.2), the lifting of the Dirichlet data and the right-hand side. */
+int tt_problem_create(tt_ctx* ctx, const tt_problem_desc* desc, tt_problem** out);
+int tt_problem_destroy(tt_problem* prob);
+/* n_u = 2 n_v free velocity dofs, n_p pressure dofs, n_xi, n_t. */
+int tt_problem_sizes(const tt_problem* prob, int* n_u, int* n_p, int* n_v, int* n_xi,
+                     int* n_t, int* n_nodes);
+/* Copy out an assembled scalar matrix in CSR form over free dofs (rows) and
+ * free (block 0) or Dirichlet (block 1) columns, for verification.  which:
+ * 0 = M, 1 + l = A_l, 100 = B_x1, 101 = B_x2 (pressure rows).  Pass NULL
+ * buffers to query nnz / rows first. */
+int tt_problem_matrix(tt_ctx* ctx, const tt_problem* prob, int which, int block,
+                      int* n_rows, int* n_cols, int* nnz, int* rowptr, int* colidx,
+                      double* vals);
+
+/* Right-hand side f = (f^u, f^p) of the all-at-once system (Dirichlet data). */
+int tt_rhs(tt_ctx* ctx, tt_problem* prob, tt_t** fu, tt_t** fp);
+/* Full-node velocity w = E u + u_D (n_x = 2 n_nodes, ranks + 1). */
+int tt_full_velocity(tt_ctx* ctx, tt_problem* prob, const tt_t* u, tt_t** w);
+
+/* ---- operators (eq. F, eq. N_kron, Section 5.2) ------------------------------ */
+
+enum { TT_OP_FULL = 0, TT_OP_MEAN = 1 };
+
+/* Operator of the linear system at a Picard step: FULL is
+ * [[F(w) + C, B^T], [B, 0]]; MEAN is the velocity block F_0 + C of Section 5.2.
+ * w: full-node convection train (tt_full_velocity, usually truncated), or NULL
+ * for the Stokes problem (N = 0).  The operator keeps a copy of what it needs,
+ * including the preconditioner factors of Section 5 (built on first use). */
+int tt_op_create(tt_ctx* ctx, tt_problem* prob, const tt_t* w, int which, tt_op** out);
+int tt_op_destroy(tt_op* op);
+
+/* (out_u, out_p) = L [u; p] for a FULL operator (p may not be NULL), or
+ * out_u = (F_0 + C) u for a MEAN operator (p, out_p ignored).  eps > 0 rounds
+ * each output train with T_eps. */
+int tt_matvec(tt_ctx* ctx, const tt_op* op, const tt_t* u, const tt_t* p, double eps,
+              tt_t** out_u, tt_t** out_p);
+
+/* Mean-based block triangular preconditioner of eq. (prec) with the LSC Schur
+ * approximation of eq. (mean_lsc) and the inner low-rank GMRES solve of
+ * eq. (11_sys) preconditioned by eq. (11_prec), applied to (a_u, a_p). */
+int tt_prec_apply(tt_ctx* ctx, tt_op* op, const tt_t* au, const tt_t* ap, double eps,
+                  double tol_inner, int maxit_inner, tt_t** u, tt_t** p, int* inner_its);
+
+/* Nonlinear residual r = f - A(w)[u; p], w = E u + u_D untruncated
+ * (Section 4.3), truncated with eps; *norm = ||T(r)||. */
+int tt_residual(tt_ctx* ctx, tt_problem* prob, const tt_t* u, const tt_t* p, double eps,
+                tt_t** ru, tt_t** rp, double* norm);
+
+/* ---- solvers (Algorithms 4.2, 3.1) ----------------------------------------- */
+
+typedef struct {
+    double tol_picard;   /* Picard stopping ||r|| <= tol_picard ||f|| */
+    double tol_gmres;    /* outer GMRES stopping, relative to ||b|| */
+    double eps_gmres;    /* truncation in GMRES (and the inner solve) */
+    double eps_soln;     /* truncation of the Picard iterates, eq. (eps_soln) */
+    double eps_conv;     /* truncation of the convection field, eq. (eps_conv) */
+    double tol_inner;    /* inner (F_0 + C) solve stopping, Section 5.3 */
+    int maxit_picard, maxit_gmres, maxit_inner;
+} tt_solver_opts;
+
+typedef struct {
+    int its;             /* iterations taken */
+    double res0;         /* ||s_0|| */
+    double res;          /* ||s_k|| at exit */
+    int inner_its;       /* total inner iterations of the preconditioner */
+} tt_gmres_stats;
+
+#define TT_MAX_PICARD 64
+typedef struct {
+    int picard_its;
+    int stokes_its;
+    double fnorm;
+    double res[TT_MAX_PICARD + 1];        /* ||r^(i)||, i = 0..picard_its */
+    int gmres_its[TT_MAX_PICARD + 1];     /* per Picard step (index 0: Stokes) */
+    int inner_its[TT_MAX_PICARD + 1];
+    int ranks[TT_MAX_PICARD + 1][4];      /* u (k1,k2), p (k1,k2) after each step */
+    int conv_ranks[TT_MAX_PICARD + 1][2]; /* truncated convection field */
+} tt_picard_stats;
+
+/* Low-rank flexible GMRES (Algorithm 4.2) for op [z_u; z_p] = [b_u; b_p] with
+ * the preconditioner above, z_0 = 0, stop when ||s_k|| <= tol_gmres * bnorm
+ * (bnorm <= 0: use ||b||).  Returns TT_ENOCONV (with the last iterate) if
+ * maxit_gmres is reached first. */
+int tt_gmres(tt_ctx* ctx, tt_op* op, const tt_solver_opts* opts, const tt_t* bu,
+             const tt_t* bp, double bnorm, tt_t** zu, tt_t** zp, tt_gmres_stats* stats);
+
+/* Truncated inexact Picard iteration (Algorithm 3.1, eq. eps_soln, eq. eps_conv,
+ * Section 5.2): Stokes initial iterate, then correction solves until
+ * ||r|| <= tol_picard ||f||.  Returns the velocity and pressure trains. */
+int picard_solve(tt_ctx* ctx, tt_problem* prob, const tt_solver_opts* opts, tt_t** u,
+                 tt_t** p, tt_picard_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TT_STOCHNS_H */

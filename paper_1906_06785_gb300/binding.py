@@ -1,0 +1,376 @@
+"""ctypes binding of include/tt_stochns.h (argument marshalling only).
+
+Every computation runs in libttns.so on the GPU.  Importing this module does
+not touch the GPU; `Context()` does, and raises if the library is missing or
+no CUDA device is present.  Cores cross the boundary in the paper's shapes
+(z1: n_t x r1, z2: r1 x n_xi x r2, z3: r2 x n_x) as numpy float64 arrays; the
+binding converts to and from the library's layouts.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libttns.so")
+
+TT_OK, TT_EINVAL, TT_ENOMEM, TT_ECUDA, TT_ENOCONV, TT_ERANK, TT_ENAN, TT_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
+OP_FULL, OP_MEAN = 0, 1
+MAX_PICARD = 64
+
+_P = C.c_void_p
+_D = C.c_double
+_I = C.c_int
+_DP = C.POINTER(C.c_double)
+_IP = C.POINTER(C.c_int)
+
+
+class ProblemDesc(C.Structure):
+    _fields_ = [("n_nodes", _I), ("n_elem", _I), ("n_pnodes", _I), ("h", _D),
+                ("xy", _DP), ("elem_q2", C.POINTER(C.c_longlong)), ("elem_q1", C.POINTER(C.c_longlong)),
+                ("dirichlet", C.POINTER(C.c_ubyte)), ("inflow", _DP), ("m", _I), ("n_xi", _I),
+                ("multi_index", C.POINTER(C.c_longlong)), ("nu", _DP), ("n_t", _I), ("tau", _D),
+                ("tprofile", _DP)]
+
+
+class SolverOpts(C.Structure):
+    _fields_ = [("tol_picard", _D), ("tol_gmres", _D), ("eps_gmres", _D), ("eps_soln", _D),
+                ("eps_conv", _D), ("tol_inner", _D), ("maxit_picard", _I), ("maxit_gmres", _I),
+                ("maxit_inner", _I)]
+
+
+class GmresStats(C.Structure):
+    _fields_ = [("its", _I), ("res0", _D), ("res", _D), ("inner_its", _I)]
+
+
+class PicardStats(C.Structure):
+    _fields_ = [("picard_its", _I), ("stokes_its", _I), ("fnorm", _D),
+                ("res", _D * (MAX_PICARD + 1)), ("gmres_its", _I * (MAX_PICARD + 1)),
+                ("inner_its", _I * (MAX_PICARD + 1)), ("ranks", (_I * 4) * (MAX_PICARD + 1)),
+                ("conv_ranks", (_I * 2) * (MAX_PICARD + 1))]
+
+
+_SIGS = {
+    "tt_ctx_create": (_I, [_P, C.POINTER(_P)]),
+    "tt_ctx_destroy": (_I, [_P]),
+    "tt_last_error": (C.c_char_p, [_P]),
+    "tt_ctx_launches": (C.c_longlong, [_P]),
+    "tt_ctx_profile": (_I, [_P, _I]),
+    "tt_ctx_prof_read": (_I, [_P, _I, C.POINTER(C.c_longlong), _DP, _DP, _DP]),
+    "tt_create": (_I, [_P, _I, _I, _I, _I, _I, _P, _P, _P, _I, C.POINTER(_P)]),
+    "tt_destroy": (_I, [_P]),
+    "tt_shape": (_I, [_P, _IP, _IP, _IP, _IP, _IP]),
+    "tt_get_cores": (_I, [_P, _P, _P, _P, _P, _I]),
+    "tt_round": (_I, [_P, _P, _D, C.POINTER(_P), _DP, _DP]),
+    "tt_dot": (_I, [_P, _P, _P, _DP]),
+    "tt_axpby": (_I, [_P, _D, _P, _D, _P, C.POINTER(_P)]),
+    "tt_problem_create": (_I, [_P, C.POINTER(ProblemDesc), C.POINTER(_P)]),
+    "tt_problem_destroy": (_I, [_P]),
+    "tt_problem_sizes": (_I, [_P, _IP, _IP, _IP, _IP, _IP, _IP]),
+    "tt_problem_matrix": (_I, [_P, _P, _I, _I, _IP, _IP, _IP, _IP, _IP, _DP]),
+    "tt_rhs": (_I, [_P, _P, C.POINTER(_P), C.POINTER(_P)]),
+    "tt_full_velocity": (_I, [_P, _P, _P, C.POINTER(_P)]),
+    "tt_op_create": (_I, [_P, _P, _P, _I, C.POINTER(_P)]),
+    "tt_op_destroy": (_I, [_P]),
+    "tt_matvec": (_I, [_P, _P, _P, _P, _D, C.POINTER(_P), C.POINTER(_P)]),
+    "tt_prec_apply": (_I, [_P, _P, _P, _P, _D, _D, _I, C.POINTER(_P), C.POINTER(_P), _IP]),
+    "tt_residual": (_I, [_P, _P, _P, _P, _D, C.POINTER(_P), C.POINTER(_P), _DP]),
+    "tt_gmres": (_I, [_P, _P, C.POINTER(SolverOpts), _P, _P, _D, C.POINTER(_P), C.POINTER(_P),
+                      C.POINTER(GmresStats)]),
+    "picard_solve": (_I, [_P, _P, C.POINTER(SolverOpts), C.POINTER(_P), C.POINTER(_P),
+                          C.POINTER(PicardStats)]),
+}
+
+
+class LibraryError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libttns error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libttns.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"GPU library not built: {path} (run paper_1906_06785_gb300.build)")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+class Context:
+    """A library context bound to a CUDA stream (torch's current stream by default)."""
+
+    def __init__(self, stream=None):
+        self.lib = load()
+        if stream is None:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("no CUDA device: the GPU library has no CPU fallback")
+            stream = torch.cuda.current_stream().cuda_stream
+        h = _P()
+        self._check(self.lib.tt_ctx_create(_P(stream), C.byref(h)), None)
+        self.h = h
+
+    def _check(self, code, h=True):
+        if code != TT_OK:
+            msg = self.lib.tt_last_error(self.h if h else None)
+            raise LibraryError(code, msg.decode() if msg else "")
+
+    def check(self, code, allow=()):
+        if code != TT_OK and code not in allow:
+            self._check(code)
+        return code
+
+    @property
+    def launches(self):
+        return int(self.lib.tt_ctx_launches(self.h))
+
+    PROF_SLOTS = ("qr", "jacobi", "gemm", "spmm", "band_solve", "band_factor", "core", "assembly")
+
+    def profile(self, enable=True):
+        """Reset the per-kernel-class counters and turn event timing on or off."""
+        self.check(self.lib.tt_ctx_profile(self.h, 1 if enable else 0))
+
+    def prof_read(self):
+        """{class: (launches, ms, flops, bytes)} since the last profile() call."""
+        out = {}
+        for i, name in enumerate(self.PROF_SLOTS):
+            n = C.c_longlong(); ms = _D(); fl = _D(); by = _D()
+            self.check(self.lib.tt_ctx_prof_read(self.h, i, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by)))
+            out[name] = (n.value, ms.value, fl.value, by.value)
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tt_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- trains ------------------------------------------------------------
+    def tt(self, z1, z2, z3):
+        """New device train from cores in the paper's shapes (numpy)."""
+        z1 = np.asarray(z1, np.float64); z2 = np.asarray(z2, np.float64); z3 = np.asarray(z3, np.float64)
+        n_t, r1 = z1.shape
+        r1b, n_xi, r2 = z2.shape
+        r2b, n_x = z3.shape
+        if r1 != r1b or r2 != r2b:
+            raise ValueError("inconsistent ranks")
+        a1 = np.ascontiguousarray(z1.T)
+        a2 = np.ascontiguousarray(z2)
+        a3 = np.ascontiguousarray(z3.T)
+        h = _P()
+        self.check(self.lib.tt_create(self.h, n_t, n_xi, n_x, r1, r2, a1.ctypes.data, a2.ctypes.data,
+                                      a3.ctypes.data, 0, C.byref(h)))
+        return TTHandle(self, h)
+
+    def round(self, t, eps):
+        out = _P(); nb = _D(); na = _D()
+        self.check(self.lib.tt_round(self.h, t.h, eps, C.byref(out), C.byref(nb), C.byref(na)))
+        return TTHandle(self, out), nb.value, na.value
+
+    def dot(self, a, b):
+        out = _D()
+        self.check(self.lib.tt_dot(self.h, a.h, b.h, C.byref(out)))
+        return out.value
+
+    def axpby(self, alpha, a, beta, b):
+        out = _P()
+        self.check(self.lib.tt_axpby(self.h, alpha, a.h, beta, b.h, C.byref(out)))
+        return TTHandle(self, out)
+
+    # ---- problem -------------------------------------------------------------
+    def problem(self, prob):
+        return ProblemHandle(self, prob)
+
+
+class TTHandle:
+    def __init__(self, ctx, h):
+        self.ctx, self.h = ctx, h
+
+    def shape(self):
+        v = [_I() for _ in range(5)]
+        self.ctx.check(self.ctx.lib.tt_shape(self.h, *[C.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    @property
+    def ranks(self):
+        s = self.shape()
+        return (s[3], s[4])
+
+    def cores(self):
+        n_t, n_xi, n_x, r1, r2 = self.shape()
+        a1 = np.empty((r1, n_t)); a2 = np.empty((r1, n_xi, r2)); a3 = np.empty((n_x, r2))
+        self.ctx.check(self.ctx.lib.tt_get_cores(self.ctx.h, self.h, a1.ctypes.data, a2.ctypes.data,
+                                                 a3.ctypes.data, 0))
+        return a1.T.copy(), a2, a3.T.copy()
+
+    def full(self):
+        z1, z2, z3 = self.cores()
+        return np.einsum("ia,ajb,bk->ijk", z1, z2, z3)
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.tt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def opts_from(tol, **over):
+    o = SolverOpts(tol_picard=tol.tol_picard, tol_gmres=tol.tol_gmres, eps_gmres=tol.eps_gmres,
+                   eps_soln=tol.eps_soln, eps_conv=tol.eps_conv, tol_inner=tol.tol_inner,
+                   maxit_picard=tol.maxit_picard, maxit_gmres=tol.maxit_gmres, maxit_inner=tol.maxit_inner)
+    for k, v in over.items():
+        setattr(o, k, v)
+    return o
+
+
+class ProblemHandle:
+    """Device discretisation built from a `synth.Problem` (arrays copied by the library)."""
+
+    def __init__(self, ctx, prob):
+        self.ctx = ctx
+        self.prob = prob
+        m = prob.mesh
+        self._keep = dict(
+            xy=np.ascontiguousarray(m.xy, np.float64),
+            q2=np.ascontiguousarray(m.elem_q2, np.int64),
+            q1=np.ascontiguousarray(m.elem_q1, np.int64),
+            dir=np.ascontiguousarray(m.dirichlet.astype(np.uint8)),
+            inflow=np.ascontiguousarray(m.inflow, np.float64),
+            mi=np.ascontiguousarray(prob.mi, np.int64),
+            nu=np.ascontiguousarray(prob.nu, np.float64),
+            tp=np.ascontiguousarray(prob.tprofile, np.float64))
+        k = self._keep
+        d = ProblemDesc(n_nodes=m.n_nodes, n_elem=m.n_elem, n_pnodes=m.n_pnodes, h=m.h,
+                        xy=k["xy"].ctypes.data_as(_DP),
+                        elem_q2=k["q2"].ctypes.data_as(C.POINTER(C.c_longlong)),
+                        elem_q1=k["q1"].ctypes.data_as(C.POINTER(C.c_longlong)),
+                        dirichlet=k["dir"].ctypes.data_as(C.POINTER(C.c_ubyte)),
+                        inflow=k["inflow"].ctypes.data_as(_DP), m=prob.m, n_xi=prob.n_xi,
+                        multi_index=k["mi"].ctypes.data_as(C.POINTER(C.c_longlong)),
+                        nu=k["nu"].ctypes.data_as(_DP), n_t=prob.n_t, tau=prob.tau,
+                        tprofile=k["tp"].ctypes.data_as(_DP))
+        h = _P()
+        ctx.check(ctx.lib.tt_problem_create(ctx.h, C.byref(d), C.byref(h)))
+        self.h = h
+
+    def sizes(self):
+        v = [_I() for _ in range(6)]
+        self.ctx.check(self.ctx.lib.tt_problem_sizes(self.h, *[C.byref(x) for x in v]))
+        return dict(zip(("n_u", "n_p", "n_v", "n_xi", "n_t", "n_nodes"), (x.value for x in v)))
+
+    def matrix(self, which, block=0):
+        """(rowptr, col, vals, shape) of an assembled matrix (see tt_problem_matrix)."""
+        nr, nc, nnz = _I(), _I(), _I()
+        lib = self.ctx.lib
+        self.ctx.check(lib.tt_problem_matrix(self.ctx.h, self.h, which, block, C.byref(nr), C.byref(nc),
+                                             C.byref(nnz), None, None, None))
+        rp = np.empty(nr.value + 1, np.int32); cl = np.empty(max(nnz.value, 1), np.int32)
+        vals = np.empty(max(nnz.value, 1))
+        self.ctx.check(lib.tt_problem_matrix(self.ctx.h, self.h, which, block, None, None, None,
+                                             rp.ctypes.data_as(_IP), cl.ctypes.data_as(_IP),
+                                             vals.ctypes.data_as(_DP)))
+        return rp, cl[:nnz.value], vals[:nnz.value], (nr.value, nc.value)
+
+    def rhs(self):
+        a, b = _P(), _P()
+        self.ctx.check(self.ctx.lib.tt_rhs(self.ctx.h, self.h, C.byref(a), C.byref(b)))
+        return TTHandle(self.ctx, a), TTHandle(self.ctx, b)
+
+    def full_velocity(self, u):
+        w = _P()
+        self.ctx.check(self.ctx.lib.tt_full_velocity(self.ctx.h, self.h, u.h, C.byref(w)))
+        return TTHandle(self.ctx, w)
+
+    def op(self, w=None, which=OP_FULL):
+        h = _P()
+        self.ctx.check(self.ctx.lib.tt_op_create(self.ctx.h, self.h, w.h if w is not None else None, which,
+                                                 C.byref(h)))
+        return OpHandle(self.ctx, h, which)
+
+    def residual(self, u, p, eps):
+        a, b, n = _P(), _P(), _D()
+        self.ctx.check(self.ctx.lib.tt_residual(self.ctx.h, self.h, u.h, p.h, eps, C.byref(a), C.byref(b),
+                                                C.byref(n)))
+        return TTHandle(self.ctx, a), TTHandle(self.ctx, b), n.value
+
+    def picard(self, opts):
+        a, b = _P(), _P()
+        st = PicardStats()
+        code = self.ctx.check(self.ctx.lib.picard_solve(self.ctx.h, self.h, C.byref(opts), C.byref(a),
+                                                        C.byref(b), C.byref(st)), allow=(TT_ENOCONV,))
+        return TTHandle(self.ctx, a), TTHandle(self.ctx, b), st, code
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.tt_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class OpHandle:
+    def __init__(self, ctx, h, which):
+        self.ctx, self.h, self.which = ctx, h, which
+
+    def matvec(self, u, p=None, eps=0.0):
+        a, b = _P(), _P()
+        self.ctx.check(self.ctx.lib.tt_matvec(self.ctx.h, self.h, u.h, p.h if p is not None else None, eps,
+                                              C.byref(a), C.byref(b) if self.which == OP_FULL else None))
+        if self.which == OP_FULL:
+            return TTHandle(self.ctx, a), TTHandle(self.ctx, b)
+        return TTHandle(self.ctx, a)
+
+    def prec(self, au, ap, eps, tol_inner, maxit_inner):
+        a, b, its = _P(), _P(), _I()
+        self.ctx.check(self.ctx.lib.tt_prec_apply(self.ctx.h, self.h, au.h, ap.h, eps, tol_inner, maxit_inner,
+                                                  C.byref(a), C.byref(b), C.byref(its)))
+        return TTHandle(self.ctx, a), TTHandle(self.ctx, b), its.value
+
+    def gmres(self, opts, bu, bp, bnorm=0.0):
+        a, b = _P(), _P()
+        st = GmresStats()
+        code = self.ctx.check(self.ctx.lib.tt_gmres(self.ctx.h, self.h, C.byref(opts), bu.h, bp.h, bnorm,
+                                                    C.byref(a), C.byref(b), C.byref(st)), allow=(TT_ENOCONV,))
+        return TTHandle(self.ctx, a), TTHandle(self.ctx, b), st, code
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.tt_op_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

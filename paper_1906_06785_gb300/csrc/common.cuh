@@ -1,0 +1,216 @@
+// Shared host/device infrastructure of the GPU solver: context, errors,
+// stream-ordered device buffers, launch accounting and the bounded grid-wide
+// barrier used by the cooperative (persistent) kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/tt_stochns.h"
+
+namespace tt {
+
+// ---------------------------------------------------------------- errors
+struct Error : std::runtime_error {
+    int code;
+    Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define TT_THROW(code, ...)                                      \
+    do {                                                         \
+        char _b[400];                                            \
+        snprintf(_b, sizeof(_b), __VA_ARGS__);                   \
+        throw ::tt::Error((code), std::string(_b));              \
+    } while (0)
+
+#define TT_REQUIRE(cond, ...)                                    \
+    do {                                                         \
+        if (!(cond)) TT_THROW(TT_EINVAL, __VA_ARGS__);           \
+    } while (0)
+
+#define CUDA_CHECK(expr)                                                              \
+    do {                                                                              \
+        cudaError_t _e = (expr);                                                      \
+        if (_e != cudaSuccess)                                                        \
+            TT_THROW(_e == cudaErrorMemoryAllocation ? TT_ENOMEM : TT_ECUDA,          \
+                     "%s:%d %s: %s", __FILE__, __LINE__, #expr, cudaGetErrorString(_e)); \
+    } while (0)
+
+// Device status word written by kernels whose waits are bounded.
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_NAN = 2 };
+
+}  // namespace tt
+
+// ---------------------------------------------------------------- profiling
+// Opt-in per-kernel-class timing with CUDA events on the context stream, plus
+// the algorithmic flops and bytes of every timed launch.
+enum ProfSlot : int {
+    PROF_QR = 0, PROF_JACOBI, PROF_GEMM, PROF_SPMM, PROF_BAND_SOLVE, PROF_BAND_FACTOR,
+    PROF_CORE, PROF_ASSEMBLY, PROF_NSLOTS
+};
+struct ProfData {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[PROF_NSLOTS];
+    std::vector<cudaEvent_t> pool;
+    double ms[PROF_NSLOTS] = {0};
+    double flops[PROF_NSLOTS] = {0};
+    double bytes[PROF_NSLOTS] = {0};
+    long long n[PROF_NSLOTS] = {0};
+};
+
+// ---------------------------------------------------------------- context
+struct tt_ctx {
+    bool prof = false;
+    ProfData pd;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int nsm = 0;
+    long long launches = 0;
+    std::string err = "ok";
+    // small pinned host buffer for scalar read-back
+    void* pinned = nullptr;
+    // device status word (bounded waits) + barrier counters
+    int* dstatus = nullptr;
+    unsigned* dbarrier = nullptr;   // [count, generation] per barrier slot
+};
+
+namespace tt {
+
+inline void count_launch(tt_ctx* c, int n = 1) { c->launches += n; }
+
+#define LAUNCH_CHECK(ctx)                                                         \
+    do {                                                                          \
+        ::tt::count_launch(ctx);                                                  \
+        cudaError_t _e = cudaGetLastError();                                      \
+        if (_e != cudaSuccess)                                                    \
+            TT_THROW(TT_ECUDA, "%s:%d launch: %s", __FILE__, __LINE__, cudaGetErrorString(_e)); \
+    } while (0)
+
+// Stream-ordered device buffer (cudaMallocAsync pool on the context stream).
+template <typename T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    cudaStream_t s = nullptr;
+    DBuf() = default;
+    DBuf(tt_ctx* c, size_t count) { alloc(c, count); }
+    void alloc(tt_ctx* c, size_t count) {
+        release();
+        s = c->stream;
+        n = count;
+        if (count) CUDA_CHECK(cudaMallocAsync((void**)&p, count * sizeof(T), s));
+    }
+    void release() {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        n = 0;
+    }
+    ~DBuf() { release(); }
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; o.n = 0; }
+    DBuf& operator=(DBuf&& o) noexcept {
+        release();
+        p = o.p; n = o.n; s = o.s;
+        o.p = nullptr; o.n = 0;
+        return *this;
+    }
+};
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Copy scalars device -> host through the pinned buffer (synchronises the stream).
+template <typename T>
+inline void read_back(tt_ctx* c, const T* dsrc, T* hdst, size_t n) {
+    size_t bytes = n * sizeof(T);
+    if (bytes > 4096) {
+        CUDA_CHECK(cudaMemcpyAsync(hdst, dsrc, bytes, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_CHECK(cudaStreamSynchronize(c->stream));
+        return;
+    }
+    CUDA_CHECK(cudaMemcpyAsync(c->pinned, dsrc, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    memcpy(hdst, c->pinned, bytes);
+}
+
+// Check the device status word after kernels with bounded waits.
+void check_status(tt_ctx* c);
+
+// Records an event pair around the launches in its scope when profiling is on.
+struct ProfScope {
+    tt_ctx* c;
+    int slot;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(tt_ctx* ctx, int s, double flops, double bytes);
+    ~ProfScope();
+};
+void prof_resolve(tt_ctx* c);
+
+}  // namespace tt
+
+// ---------------------------------------------------------------- tensor train
+// Device-resident train, layouts as in include/tt_stochns.h.
+struct tt_t {
+    tt_ctx* ctx = nullptr;
+    int n_t = 0, n_xi = 0, n_x = 0, r1 = 0, r2 = 0;
+    double* base = nullptr;
+    double* z1 = nullptr;   // [r1][n_t]
+    double* z2 = nullptr;   // [r1][n_xi][r2]
+    double* z3 = nullptr;   // [n_x][r2]
+};
+
+namespace tt {
+
+tt_t* tt_alloc(tt_ctx* c, int n_t, int n_xi, int n_x, int r1, int r2);
+void tt_free(tt_t* t);
+using TTPtr = std::unique_ptr<tt_t, void (*)(tt_t*)>;
+inline TTPtr wrap(tt_t* t) { return TTPtr(t, tt_free); }
+
+// ---------------------------------------------------------------- device helpers
+#ifdef __CUDACC__
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Grid-wide barrier for cooperative launches.  bar[0] counts arrivals, bar[1] is
+// the generation.  Every wait is bounded: after `limit` polls the block records
+// DEV_TIMEOUT in *status and leaves; once the status is set, later barriers
+// return at once, so a kernel that lost a block still terminates.
+__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = bar + 1;
+        unsigned gen = *vgen;
+        __threadfence();
+        unsigned arrived = atomicAdd(bar, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long polls = 0;
+            const long long limit = 20000000LL;   // ~ seconds with backoff
+            while (*vgen == gen) {
+                if (*(volatile int*)status != DEV_OK) break;
+                if (++polls > limit) {
+                    atomicExch(status, DEV_TIMEOUT);
+                    break;
+                }
+                if (polls > 64) __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+#endif
+
+}  // namespace tt

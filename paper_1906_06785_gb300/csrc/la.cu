@@ -1,0 +1,517 @@
+// Dense FP64 kernels of the TT rounding (Section 4.1).
+//
+//  * gemm: 64x64x16 tiles with arbitrary strides; split-K over the grid when the
+//    output has few tiles, because GB300's FP64 pipe is narrow per SM and a
+//    small product must still spread over every SM.
+//  * qr_r: R factor of a tall n x c matrix by Householder reflections, one
+//    cooperative launch.  Each CTA keeps a block of rows resident (shared
+//    memory when it fits) and, per column, the CTAs exchange partial norms and
+//    partial reflector dots through global memory across bounded grid
+//    barriers (a flat-tree TSQR in which the tree is one reduction level).
+//  * left_svd: one-sided (Hestenes) Jacobi, columns rotated pairwise in
+//    round-robin order, one warp per pair, one grid barrier per round.
+#include <algorithm>
+#include <cmath>
+
+#include "la.cuh"
+
+namespace tt {
+
+// ============================================================== GEMM
+namespace {
+constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
+
+__global__ void __launch_bounds__(256)
+k_gemm(int M, int N, int K, double alpha, const double* __restrict__ A, long long as0,
+       long long as1, const double* __restrict__ B, long long bs0, long long bs1, double beta,
+       double* __restrict__ C, long long cs0, long long cs1, int kchunk, double* __restrict__ part) {
+    __shared__ double As[GB_K][GB_M + 1];
+    __shared__ double Bs[GB_K][GB_N + 1];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int i0 = blockIdx.y * GB_M, j0 = blockIdx.x * GB_N;
+    const int kbeg = blockIdx.z * kchunk;
+    const int kend = min(K, kbeg + kchunk);
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    const bool a_rowfast = (as1 == 1);   // k contiguous: iterate k fastest
+    const bool b_colfast = (bs1 == 1);   // j contiguous: iterate j fastest
+    for (int k0 = kbeg; k0 < kend; k0 += GB_K) {
+        for (int e = tid; e < GB_M * GB_K; e += 256) {
+            int ii, kk;
+            if (a_rowfast) { kk = e % GB_K; ii = e / GB_K; } else { ii = e % GB_M; kk = e / GB_M; }
+            const int gi = i0 + ii, gk = k0 + kk;
+            As[kk][ii] = (gi < M && gk < kend) ? A[gi * as0 + gk * as1] : 0.0;
+        }
+        for (int e = tid; e < GB_K * GB_N; e += 256) {
+            int jj, kk;
+            if (b_colfast) { jj = e % GB_N; kk = e / GB_N; } else { kk = e % GB_K; jj = e / GB_K; }
+            const int gj = j0 + jj, gk = k0 + kk;
+            Bs[kk][jj] = (gj < N && gk < kend) ? B[gk * bs0 + gj * bs1] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GB_K; ++kk) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[kk][ty * 4 + a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx * 4 + b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int gi = i0 + ty * 4 + a;
+        if (gi >= M) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int gj = j0 + tx * 4 + b;
+            if (gj >= N) continue;
+            if (part) {
+                part[((size_t)blockIdx.z * M + gi) * N + gj] = acc[a][b];
+            } else {
+                double* cp = C + gi * cs0 + gj * cs1;
+                *cp = beta == 0.0 ? alpha * acc[a][b] : alpha * acc[a][b] + beta * *cp;
+            }
+        }
+    }
+}
+
+__global__ void k_gemm_reduce(int M, int N, int S, double alpha, const double* __restrict__ part,
+                              double beta, double* __restrict__ C, long long cs0, long long cs1) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)M * N) return;
+    const int i = (int)(idx / N), j = (int)(idx % N);
+    double s = 0.0;
+    for (int z = 0; z < S; ++z) s += part[(size_t)z * M * N + idx];
+    double* cp = C + i * cs0 + j * cs1;
+    *cp = beta == 0.0 ? alpha * s : alpha * s + beta * *cp;
+}
+}  // namespace
+
+void gemm(tt_ctx* c, int M, int N, int K, double alpha, MatView A, MatView B, double beta,
+          MatViewMut C) {
+    if (M <= 0 || N <= 0) return;
+    if (K <= 0) {
+        // C = beta C
+        if (beta == 0.0) {
+            copy_mat(c, M, N, MatView{C.p, C.s0, C.s1}, C, 0.0);
+        } else if (beta != 1.0) {
+            copy_mat(c, M, N, MatView{C.p, C.s0, C.s1}, C, beta);
+        }
+        return;
+    }
+    const int tm = ceil_div(M, GB_M), tn = ceil_div(N, GB_N);
+    const int tiles = tm * tn;
+    int S = 1;
+    const int target = 2 * c->nsm;
+    if (tiles < target && K > 2 * GB_K) {
+        S = std::min(ceil_div(target, tiles), ceil_div(K, 4 * GB_K));
+        S = std::max(S, 1);
+    }
+    const int kchunk = ceil_div(ceil_div(K, S), GB_K) * GB_K;
+    S = ceil_div(K, kchunk);
+    dim3 grid(tn, tm, S);
+    ProfScope prof(c, PROF_GEMM, 2.0 * M * N * K, 8.0 * ((double)M * K + (double)K * N + (double)M * N));
+    if (S == 1) {
+        k_gemm<<<grid, 256, 0, c->stream>>>(M, N, K, alpha, A.p, A.s0, A.s1, B.p, B.s0, B.s1, beta,
+                                            C.p, C.s0, C.s1, kchunk, nullptr);
+        LAUNCH_CHECK(c);
+    } else {
+        DBuf<double> part(c, (size_t)S * M * N);
+        k_gemm<<<grid, 256, 0, c->stream>>>(M, N, K, alpha, A.p, A.s0, A.s1, B.p, B.s0, B.s1, beta,
+                                            C.p, C.s0, C.s1, kchunk, part.p);
+        LAUNCH_CHECK(c);
+        const long long tot = (long long)M * N;
+        k_gemm_reduce<<<ceil_div(tot, 256), 256, 0, c->stream>>>(M, N, S, alpha, part.p, beta, C.p,
+                                                                  C.s0, C.s1);
+        LAUNCH_CHECK(c);
+    }
+}
+
+// ============================================================== copies
+namespace {
+__global__ void k_copy_mat(int m, int n, const double* __restrict__ A, long long a0, long long a1,
+                           double* __restrict__ B, long long b0, long long b1, double alpha) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)m * n) return;
+    int i, j;
+    if (b0 == 1) { i = (int)(idx % m); j = (int)(idx / m); } else { j = (int)(idx % n); i = (int)(idx / n); }
+    B[i * b0 + j * b1] = alpha == 0.0 ? 0.0 : alpha * A[i * a0 + j * a1];
+}
+}  // namespace
+
+void copy_mat(tt_ctx* c, int m, int n, MatView A, MatViewMut B, double alpha) {
+    if (m <= 0 || n <= 0) return;
+    const long long tot = (long long)m * n;
+    k_copy_mat<<<ceil_div(tot, 256), 256, 0, c->stream>>>(m, n, A.p, A.s0, A.s1, B.p, B.s0, B.s1, alpha);
+    LAUNCH_CHECK(c);
+}
+
+void fill_zero(tt_ctx* c, double* p, size_t n) {
+    if (n) CUDA_CHECK(cudaMemsetAsync(p, 0, n * sizeof(double), c->stream));
+}
+
+// ============================================================== QR (R only)
+namespace {
+struct QRParams {
+    int n, c, k, nb, nbp;
+    const double* A;
+    long long rs, cs;
+    double* R;
+    int ldr;
+    double* gwork;
+    double* part;    // [G]
+    double* part2;   // [G][c]
+    double* wv;      // [c]
+    double* diag;    // [1]
+    unsigned* bar;
+    int* status;
+};
+
+__device__ double block_sum(double v, double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (warp == 0) {
+        s = lane < nw ? red[lane] : 0.0;
+        s = warp_sum(s);
+        if (lane == 0) red[0] = s;
+    }
+    __syncthreads();
+    s = red[0];
+    __syncthreads();
+    return s;
+}
+
+__global__ void __launch_bounds__(256) k_qr_r(QRParams P) {
+    extern __shared__ double sm[];
+    const int g = blockIdx.x, G = gridDim.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int row0 = g * P.nb;
+    const int rows = max(0, min(P.nb, P.n - row0));
+    double* v = sm;                 // [nbp]
+    double* red = sm + P.nbp;       // [32]
+    double* W = P.gwork ? P.gwork + (size_t)g * P.nbp * P.c : sm + P.nbp + 32;   // [c][nbp]
+    for (int l = warp; l < P.c; l += nw)
+        for (int i = lane; i < rows; i += 32)
+            W[(size_t)l * P.nbp + i] = P.A[(long long)(row0 + i) * P.rs + (long long)l * P.cs];
+    __syncthreads();
+
+    for (int j = 0; j < P.k; ++j) {
+        if (*(volatile int*)P.status != DEV_OK) return;
+        const int jloc = j - row0;
+        const bool own = (jloc >= 0 && jloc < rows);
+        // A: partial sum of squares of column j strictly below row j, and the diagonal
+        double ss = 0.0;
+        for (int i = max(0, j + 1 - row0) + tid; i < rows; i += blockDim.x) {
+            const double x = W[(size_t)j * P.nbp + i];
+            ss += x * x;
+        }
+        ss = block_sum(ss, red);
+        if (tid == 0) {
+            P.part[g] = ss;
+            if (own) P.diag[0] = W[(size_t)j * P.nbp + jloc];
+        }
+        grid_barrier(P.bar, G, P.status);
+        // B: every CTA forms the same reflector (same data, same summation order)
+        if (warp == 0) {
+            double s = 0.0;
+            for (int q = lane; q < G; q += 32) s += __ldcg(P.part + q);
+            s = warp_sum(s);
+            if (lane == 0) { red[0] = s; red[1] = __ldcg(P.diag); }
+        }
+        __syncthreads();
+        const double sstail = red[0], x0 = red[1];
+        __syncthreads();
+        if (sstail == 0.0) {      // reflector is the identity
+            if (own)
+                for (int l = tid; l < P.c; l += blockDim.x)
+                    P.R[(size_t)j * P.ldr + l] = l < j ? 0.0 : W[(size_t)l * P.nbp + jloc];
+            __syncthreads();
+            continue;
+        }
+        const double sigma = sqrt(x0 * x0 + sstail);
+        const double alpha = x0 >= 0.0 ? -sigma : sigma;
+        const double v0 = x0 - alpha;
+        const double beta = 2.0 / (v0 * v0 + sstail);
+        for (int i = tid; i < rows; i += blockDim.x) {
+            const int gi = row0 + i;
+            v[i] = gi < j ? 0.0 : (gi == j ? v0 : W[(size_t)j * P.nbp + i]);
+        }
+        __syncthreads();
+        const int ib = max(0, j - row0);
+        for (int l = j + 1 + warp; l < P.c; l += nw) {
+            double p = 0.0;
+            for (int i = ib + lane; i < rows; i += 32) p += v[i] * W[(size_t)l * P.nbp + i];
+            p = warp_sum(p);
+            if (lane == 0) P.part2[(size_t)g * P.c + l] = p;
+        }
+        grid_barrier(P.bar, G, P.status);
+        // C: reduce-scatter of the reflector dots over all warps of the grid
+        const int gw = g * nw + warp, TW = G * nw;
+        for (int l = j + 1 + gw; l < P.c; l += TW) {
+            double s = 0.0;
+            for (int q = lane; q < G; q += 32) s += __ldcg(P.part2 + (size_t)q * P.c + l);
+            s = warp_sum(s);
+            if (lane == 0) P.wv[l] = beta * s;
+        }
+        grid_barrier(P.bar, G, P.status);
+        // D: apply the reflector to the trailing columns of the resident rows
+        for (int l = j + 1 + warp; l < P.c; l += nw) {
+            const double wl = __ldcg(P.wv + l);
+            for (int i = ib + lane; i < rows; i += 32) W[(size_t)l * P.nbp + i] -= v[i] * wl;
+        }
+        __syncthreads();
+        if (own)
+            for (int l = tid; l < P.c; l += blockDim.x)
+                P.R[(size_t)j * P.ldr + l] = l < j ? 0.0 : (l == j ? alpha : W[(size_t)l * P.nbp + jloc]);
+        __syncthreads();
+    }
+}
+}  // namespace
+
+void qr_r(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr) {
+    TT_REQUIRE(n > 0 && cols > 0, "qr_r: empty matrix %d x %d", n, cols);
+    const int k = std::min(n, cols);
+    int G = std::min(c->nsm, std::max(1, ceil_div(n, 32)));
+    const int nb = ceil_div(n, G);
+    G = ceil_div(n, nb);
+    const int nbp = nb | 1;
+    size_t smem = (size_t)(nbp + 32) * sizeof(double);
+    const size_t wbytes = (size_t)nbp * cols * sizeof(double);
+    DBuf<double> gwork;
+    const size_t smem_limit = 200 * 1024;
+    if (smem + wbytes <= smem_limit) {
+        smem += wbytes;
+    } else {
+        gwork.alloc(c, (size_t)G * nbp * cols);
+    }
+    DBuf<double> scratch(c, (size_t)G + (size_t)G * cols + cols + 1);
+    QRParams P;
+    P.n = n; P.c = cols; P.k = k; P.nb = nb; P.nbp = nbp;
+    P.A = A.p; P.rs = A.s0; P.cs = A.s1;
+    P.R = R; P.ldr = ldr;
+    P.gwork = gwork.p;
+    P.part = scratch.p;
+    P.part2 = scratch.p + G;
+    P.wv = scratch.p + G + (size_t)G * cols;
+    P.diag = P.wv + cols;
+    P.bar = c->dbarrier;
+    P.status = c->dstatus;
+    CUDA_CHECK(cudaMemsetAsync(c->dbarrier, 0, 2 * sizeof(unsigned), c->stream));
+    CUDA_CHECK(cudaFuncSetAttribute(k_qr_r, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    // Householder R factor: 2 n c^2 - 2 c^3 / 3 flops (n >= c); reads A once, writes R
+    const double kk = k;
+    ProfScope prof(c, PROF_QR, 2.0 * kk * kk * ((double)n + cols - kk) - 2.0 * kk * kk * kk / 3.0 + 0.0,
+                   8.0 * ((double)n * cols + kk * cols));
+    void* args[] = {&P};
+    CUDA_CHECK(cudaLaunchCooperativeKernel((void*)k_qr_r, dim3(G), dim3(256), args, smem, c->stream));
+    count_launch(c);
+}
+
+// ============================================================== Jacobi SVD
+namespace {
+__global__ void __launch_bounds__(128)
+k_jacobi(int m, int n, int npad, double* W, int ldw, int* flags, int max_sweeps, double tol,
+         unsigned* bar, int* status, int* sweeps_used) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int gw = blockIdx.x * nw + warp, TW = gridDim.x * nw;
+    const int P = npad / 2, NR = npad - 1;
+    int sw = 0;
+    for (; sw < max_sweeps; ++sw) {
+        int any = 0;
+        for (int r = 0; r < NR; ++r) {
+            for (int p = gw; p < P; p += TW) {
+                int a, b;
+                if (p == 0) { a = r; b = NR; } else { a = (r + p) % NR; b = (r - p + NR) % NR; }
+                if (a >= n || b >= n) continue;
+                double* ca = W + (size_t)a * ldw;
+                double* cb = W + (size_t)b * ldw;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = lane; i < m; i += 32) {
+                    const double x = __ldcg(ca + i), y = __ldcg(cb + i);
+                    al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
+                }
+                al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
+                if (al > 0.0 && be > 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+                    const double zeta = (be - al) / (2.0 * ga);
+                    const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+                    for (int i = lane; i < m; i += 32) {
+                        const double x = __ldcg(ca + i), y = __ldcg(cb + i);
+                        ca[i] = cs * x - sn * y;
+                        cb[i] = sn * x + cs * y;
+                    }
+                    any = 1;
+                }
+            }
+            grid_barrier(bar, gridDim.x, status);
+        }
+        if (any && lane == 0) flags[sw] = 1;
+        grid_barrier(bar, gridDim.x, status);
+        if (__ldcg(flags + sw) == 0) break;
+        if (*(volatile int*)status != DEV_OK) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_used = sw;
+}
+
+__global__ void k_colnorms(int m, int n, const double* __restrict__ W, int ldw, double* __restrict__ nrm) {
+    const int col = blockIdx.x;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const double x = W[(size_t)col * ldw + i];
+        s = fma(x, x, s);
+    }
+    __shared__ double red[32];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        s = warp_sum(s);
+        if (threadIdx.x == 0) nrm[col] = sqrt(s);
+    }
+}
+
+// rank[i] = position of column i in descending order (ties by index)
+__global__ void k_rank(int n, const double* __restrict__ nrm, int* __restrict__ rank) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v = nrm[i];
+        int r = 0;
+        for (int j = 0; j < n; ++j) {
+            const double w = nrm[j];
+            r += (w > v) || (w == v && j < i);
+        }
+        rank[i] = r;
+    }
+}
+
+__global__ void k_permute_normalise(int m, int n, const double* __restrict__ W, int ldw,
+                                    const double* __restrict__ nrm, const int* __restrict__ rank,
+                                    double* __restrict__ sig, double* __restrict__ U) {
+    const int col = blockIdx.x;
+    const int dst = rank[col];
+    const double s = nrm[col];
+    const double inv = s > 0.0 ? 1.0 / s : 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) U[(size_t)dst * m + i] = W[(size_t)col * ldw + i] * inv;
+    if (threadIdx.x == 0) sig[dst] = s;
+}
+}  // namespace
+
+static void jacobi_columns(tt_ctx* c, int m, int n, double* W, double* sig, double* U) {
+    // W: m x n column-major (ld m), overwritten by W V (orthogonal columns)
+    const int npad = n + (n & 1);
+    const int P = npad / 2;
+    const int wpb = 4;
+    const int G = std::max(1, std::min(c->nsm, ceil_div(P, wpb)));
+    const int max_sweeps = 60;
+    DBuf<int> flags(c, max_sweeps + 1);
+    CUDA_CHECK(cudaMemsetAsync(flags.p, 0, (max_sweeps + 1) * sizeof(int), c->stream));
+    CUDA_CHECK(cudaMemsetAsync(c->dbarrier, 0, 2 * sizeof(unsigned), c->stream));
+    double tol = std::max(1e-15, std::sqrt((double)m) * 2.220446049250313e-16);
+    int* sweeps = flags.p + max_sweeps;
+    int mm = m, nn = n, np_ = npad, ld = m, ms = max_sweeps;
+    unsigned* bar = c->dbarrier;
+    int* st = c->dstatus;
+    int* fl = flags.p;
+    void* args[] = {&mm, &nn, &np_, &W, &ld, &fl, &ms, &tol, &bar, &st, &sweeps};
+    if (n > 1) {
+        // one sweep: n(n-1)/2 pairs x (3 dots + 1 rotation) over m rows = 12 m flops per pair
+        ProfScope prof(c, PROF_JACOBI, 6.0 * n * (n - 1.0) * m, 16.0 * (double)m * n);
+        CUDA_CHECK(cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(G), dim3(32 * wpb), args, 0, c->stream));
+        count_launch(c);
+    }
+    DBuf<double> nrm(c, n);
+    DBuf<int> rank(c, n);
+    k_colnorms<<<n, 256, 0, c->stream>>>(m, n, W, m, nrm.p);
+    LAUNCH_CHECK(c);
+    k_rank<<<ceil_div(n, 256), 256, 0, c->stream>>>(n, nrm.p, rank.p);
+    LAUNCH_CHECK(c);
+    k_permute_normalise<<<n, 256, 0, c->stream>>>(m, n, W, m, nrm.p, rank.p, sig, U);
+    LAUNCH_CHECK(c);
+}
+
+void left_svd(tt_ctx* c, int m, int n, MatView A, double* sig, double* U) {
+    TT_REQUIRE(m > 0 && n > 0, "left_svd: empty matrix");
+    if (n <= m) {
+        DBuf<double> W(c, (size_t)m * n);
+        copy_mat(c, m, n, A, colmaj(W.p, m));
+        jacobi_columns(c, m, n, W.p, sig, U);
+    } else {
+        // A = R^T Q^T with A^T = Q R: left singular vectors of A are those of R^T (m x m)
+        DBuf<double> R(c, (size_t)m * m);
+        qr_r(c, n, m, trans(A), R.p, m);        // R: m x m row-major
+        DBuf<double> W(c, (size_t)m * m);
+        // W = R^T column-major: W(i, j) = R(j, i) -> element (i,j) at j*m + i = R[j*m + i]
+        CUDA_CHECK(cudaMemcpyAsync(W.p, R.p, (size_t)m * m * sizeof(double), cudaMemcpyDeviceToDevice,
+                                   c->stream));
+        jacobi_columns(c, m, m, W.p, sig, U);
+    }
+}
+
+// ============================================================== truncation
+namespace {
+__global__ void k_trunc_first(const double* __restrict__ s, int p, double eps, TruncInfo* info) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double tot = 0.0;
+    for (int i = p - 1; i >= 0; --i) tot += s[i] * s[i];
+    info->nrm = sqrt(tot);
+    const double d2 = eps > 0.0 ? 0.5 * eps * eps * tot : 0.0;
+    info->delta2 = d2;
+    int r = p;
+    if (eps > 0.0) {
+        double tail = 0.0;
+        r = p;
+        for (int i = p - 1; i >= 1; --i) {
+            tail += s[i] * s[i];
+            if (tail <= d2) r = i; else break;
+        }
+    } else {
+        r = 0;
+        for (int i = 0; i < p; ++i) r += s[i] > 0.0;
+    }
+    info->r1 = r < 1 ? 1 : r;
+}
+__global__ void k_trunc_second(const double* __restrict__ s, int p, double eps, TruncInfo* info) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double d2 = info->delta2;
+    int r = p;
+    if (eps > 0.0) {
+        double tail = 0.0;
+        for (int i = p - 1; i >= 1; --i) {
+            tail += s[i] * s[i];
+            if (tail <= d2) r = i; else break;
+        }
+    } else {
+        r = 0;
+        for (int i = 0; i < p; ++i) r += s[i] > 0.0;
+    }
+    if (r < 1) r = 1;
+    info->r2 = r;
+    double kept = 0.0;
+    for (int i = r - 1; i >= 0; --i) kept += s[i] * s[i];
+    info->nrm_after = sqrt(kept);
+}
+}  // namespace
+
+void trunc_first(tt_ctx* c, const double* sig1, int p1, double eps, TruncInfo* dinfo) {
+    k_trunc_first<<<1, 32, 0, c->stream>>>(sig1, p1, eps, dinfo);
+    LAUNCH_CHECK(c);
+}
+void trunc_second(tt_ctx* c, const double* sig2, int p2, double eps, TruncInfo* dinfo) {
+    k_trunc_second<<<1, 32, 0, c->stream>>>(sig2, p2, eps, dinfo);
+    LAUNCH_CHECK(c);
+}
+
+}  // namespace tt

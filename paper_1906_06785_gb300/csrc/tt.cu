@@ -1,0 +1,240 @@
+// Tensor trains on the device (Section 4.1): storage, concatenation (vector
+// addition), truncation T_eps and inner products.
+//
+// Truncation.  The paper's T_eps is the TT-SVD of Algorithm 4.1 applied to a
+// train: orthogonalise right to left, then truncate left to right with
+// delta = eps ||z|| / sqrt 2.  Here the orthogonalisation only forms R
+// factors (R3 of z3^T, then R of the right unfolding of z2 x3 R3), which gives
+// the singular values and left singular vectors of both unfoldings; the new
+// cores are then obtained by projecting the ORIGINAL cores onto the kept left
+// singular frames (P1 = U1^T z1, C2 = P1 x1 z2, new z3 = (U2^T C2) z3).  In
+// exact arithmetic this is the same T_eps, and it needs no orthogonal factor Q.
+#include <algorithm>
+#include <cmath>
+
+#include "tt.cuh"
+
+namespace tt {
+
+tt_t* tt_alloc(tt_ctx* c, int n_t, int n_xi, int n_x, int r1, int r2) {
+    TT_REQUIRE(n_t > 0 && n_xi > 0 && n_x > 0 && r1 > 0 && r2 > 0,
+               "bad train shape %d %d %d ranks %d %d", n_t, n_xi, n_x, r1, r2);
+    tt_t* t = new tt_t;
+    t->ctx = c;
+    t->n_t = n_t; t->n_xi = n_xi; t->n_x = n_x; t->r1 = r1; t->r2 = r2;
+    const size_t s1 = (size_t)n_t * r1, s2 = (size_t)r1 * n_xi * r2, s3 = (size_t)n_x * r2;
+    cudaError_t e = cudaMallocAsync((void**)&t->base, (s1 + s2 + s3) * sizeof(double), c->stream);
+    if (e != cudaSuccess) {
+        delete t;
+        TT_THROW(TT_ENOMEM, "train allocation of %zu doubles failed: %s", s1 + s2 + s3,
+                 cudaGetErrorString(e));
+    }
+    t->z1 = t->base;
+    t->z2 = t->base + s1;
+    t->z3 = t->base + s1 + s2;
+    return t;
+}
+
+void tt_free(tt_t* t) {
+    if (!t) return;
+    if (t->base) cudaFreeAsync(t->base, t->ctx->stream);
+    delete t;
+}
+
+TTPtr zeros(tt_ctx* c, int n_t, int n_xi, int n_x) {
+    TTPtr t = wrap(tt_alloc(c, n_t, n_xi, n_x, 1, 1));
+    fill_zero(c, t->base, (size_t)n_t + n_xi + n_x);
+    return t;
+}
+
+TTPtr clone(tt_ctx* c, const tt_t* s, double scale) {
+    TTPtr t = wrap(tt_alloc(c, s->n_t, s->n_xi, s->n_x, s->r1, s->r2));
+    const size_t tot = (size_t)s->n_t * s->r1 + (size_t)s->r1 * s->n_xi * s->r2 + (size_t)s->n_x * s->r2;
+    CUDA_CHECK(cudaMemcpyAsync(t->base, s->base, tot * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if (scale != 1.0) copy_mat(c, s->n_t, s->r1, colmaj(t->z1, s->n_t), colmaj(t->z1, s->n_t), scale);
+    return t;
+}
+
+// ============================================================== concatenation
+namespace {
+struct CatTerm {
+    const double* z1;
+    const double* z2;
+    const double* z3;
+    const double* dcoef;
+    double coef;
+    int r1, r2, off1, off2;
+};
+
+// core1: out[(off1 + a) * n_t + t] = coef * z1[a * n_t + t]
+__global__ void k_cat1(const CatTerm* __restrict__ T, int n_t, double* __restrict__ out) {
+    const CatTerm q = T[blockIdx.y];
+    const double cf = q.coef * (q.dcoef ? *q.dcoef : 1.0);
+    const int tot = n_t * q.r1;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x)
+        out[(size_t)q.off1 * n_t + e] = cf * q.z1[e];
+}
+// core2 block diagonal: out[((off1 + a) * n_xi + s) * R2 + off2 + b] = z2[(a * n_xi + s) * r2 + b]
+__global__ void k_cat2(const CatTerm* __restrict__ T, int n_xi, int R2, double* __restrict__ out) {
+    const CatTerm q = T[blockIdx.y];
+    const long long tot = (long long)q.r1 * n_xi * q.r2;
+    for (long long e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(e % q.r2);
+        const long long as = e / q.r2;
+        const int s = (int)(as % n_xi), a = (int)(as / n_xi);
+        out[((size_t)(q.off1 + a) * n_xi + s) * R2 + q.off2 + b] = q.z2[e];
+    }
+}
+// core3: out[j * R2 + off2 + b] = z3[j * r2 + b]
+__global__ void k_cat3(const CatTerm* __restrict__ T, int n_x, int R2, double* __restrict__ out) {
+    const CatTerm q = T[blockIdx.y];
+    const long long tot = (long long)n_x * q.r2;
+    for (long long e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(e % q.r2);
+        const long long j = e / q.r2;
+        out[j * R2 + q.off2 + b] = q.z3[e];
+    }
+}
+}  // namespace
+
+TTPtr concat(tt_ctx* c, const std::vector<Summand>& terms) {
+    TT_REQUIRE(!terms.empty(), "concat of nothing");
+    const tt_t* f = terms[0].t;
+    int R1 = 0, R2 = 0;
+    std::vector<CatTerm> h(terms.size());
+    for (size_t i = 0; i < terms.size(); ++i) {
+        const tt_t* t = terms[i].t;
+        TT_REQUIRE(t->n_t == f->n_t && t->n_xi == f->n_xi && t->n_x == f->n_x, "concat: shape mismatch");
+        h[i] = CatTerm{t->z1, t->z2, t->z3, terms[i].dcoef, terms[i].coef, t->r1, t->r2, R1, R2};
+        R1 += t->r1;
+        R2 += t->r2;
+    }
+    TTPtr out = wrap(tt_alloc(c, f->n_t, f->n_xi, f->n_x, R1, R2));
+    fill_zero(c, out->z2, (size_t)R1 * f->n_xi * R2);
+    DBuf<CatTerm> dT(c, h.size());
+    CUDA_CHECK(cudaMemcpyAsync(dT.p, h.data(), h.size() * sizeof(CatTerm), cudaMemcpyHostToDevice, c->stream));
+    const int nt = (int)h.size();
+    int maxr1 = 0, maxr2 = 0;
+    for (auto& q : h) { maxr1 = std::max(maxr1, q.r1); maxr2 = std::max(maxr2, q.r2); }
+    k_cat1<<<dim3(ceil_div((long long)f->n_t * maxr1, 256), nt), 256, 0, c->stream>>>(dT.p, f->n_t, out->z1);
+    LAUNCH_CHECK(c);
+    k_cat2<<<dim3(std::min(1024, ceil_div((long long)maxr1 * f->n_xi * maxr2, 256)), nt), 256, 0, c->stream>>>(
+        dT.p, f->n_xi, R2, out->z2);
+    LAUNCH_CHECK(c);
+    k_cat3<<<dim3(std::min(2048, ceil_div((long long)f->n_x * maxr2, 256)), nt), 256, 0, c->stream>>>(
+        dT.p, f->n_x, R2, out->z3);
+    LAUNCH_CHECK(c);
+    return out;
+}
+
+// ============================================================== truncation
+TTPtr round_tt(tt_ctx* c, const tt_t* z, double eps, RoundOut* info) {
+    const int n_t = z->n_t, n_xi = z->n_xi, n_x = z->n_x, R1 = z->r1, R2 = z->r2;
+    // 1. R3: R factor of z3 (n_x x R2, row-major)
+    const int k = std::min(n_x, R2);
+    DBuf<double> R3(c, (size_t)k * R2);
+    qr_r(c, n_x, R2, rowmaj(z->z3, R2), R3.p, R2);
+    // 2. Y2 = z2 x3 R3 : (R1 n_xi x R2) (R2 x k)
+    DBuf<double> Y2(c, (size_t)R1 * n_xi * k);
+    gemm(c, R1 * n_xi, k, R2, 1.0, rowmaj(z->z2, R2), trans(rowmaj(R3.p, R2)), 0.0, rowmaj(Y2.p, k));
+    // 3. Rf2: R factor of (right unfolding of Y2)^T, an (n_xi k) x R1 matrix
+    const int k1 = std::min(n_xi * k, R1);
+    DBuf<double> Rf2(c, (size_t)k1 * R1);
+    qr_r(c, n_xi * k, R1, MatView{Y2.p, 1, (long long)n_xi * k}, Rf2.p, R1);
+    // 4. A1 = z1 Rf2^T (n_t x k1): same singular values / left vectors as the first unfolding
+    DBuf<double> A1(c, (size_t)n_t * k1);
+    gemm(c, n_t, k1, R1, 1.0, colmaj(z->z1, n_t), trans(rowmaj(Rf2.p, R1)), 0.0, colmaj(A1.p, n_t));
+    // 5. left SVD, ||z||, delta, r1
+    const int p1 = std::min(n_t, k1);
+    DBuf<double> sig1(c, p1), U1(c, (size_t)n_t * p1);
+    left_svd(c, n_t, k1, colmaj(A1.p, n_t), sig1.p, U1.p);
+    DBuf<TruncInfo> dinfo(c, 1);
+    trunc_first(c, sig1.p, p1, eps, dinfo.p);
+    TruncInfo h;
+    read_back(c, dinfo.p, &h, 1);
+    check_status(c);
+    if (!(h.nrm == h.nrm) || std::isinf(h.nrm)) TT_THROW(TT_ENAN, "non-finite norm in truncation");
+    if (h.nrm == 0.0) {
+        if (info) { info->nrm_before = 0.0; info->nrm_after = 0.0; }
+        return zeros(c, n_t, n_xi, n_x);
+    }
+    const int r1 = h.r1;
+    // 6. P1 = U1_r^T z1 (r1 x R1)
+    DBuf<double> P1(c, (size_t)r1 * R1);
+    gemm(c, r1, R1, n_t, 1.0, trans(colmaj(U1.p, n_t)), colmaj(z->z1, n_t), 0.0, rowmaj(P1.p, R1));
+    // 7. C2 = P1 x1 z2 : [r1][n_xi][R2]
+    DBuf<double> C2(c, (size_t)r1 * n_xi * R2);
+    gemm(c, r1, n_xi * R2, R1, 1.0, rowmaj(P1.p, R1), rowmaj(z->z2, (long long)n_xi * R2), 0.0,
+         rowmaj(C2.p, (long long)n_xi * R2));
+    // 8. Y = C2_left R3^T (m x k), m = r1 n_xi
+    const int m = r1 * n_xi;
+    DBuf<double> Y(c, (size_t)m * k);
+    gemm(c, m, k, R2, 1.0, rowmaj(C2.p, R2), trans(rowmaj(R3.p, R2)), 0.0, colmaj(Y.p, m));
+    // 9. left SVD of Y, r2
+    const int p2 = std::min(m, k);
+    DBuf<double> sig2(c, p2), U2(c, (size_t)m * p2);
+    left_svd(c, m, k, colmaj(Y.p, m), sig2.p, U2.p);
+    trunc_second(c, sig2.p, p2, eps, dinfo.p);
+    read_back(c, dinfo.p, &h, 1);
+    check_status(c);
+    const int r2 = h.r2;
+    TTPtr out = wrap(tt_alloc(c, n_t, n_xi, n_x, r1, r2));
+    // 10. new cores 1 and 2 are the kept left singular frames
+    CUDA_CHECK(cudaMemcpyAsync(out->z1, U1.p, (size_t)n_t * r1 * sizeof(double), cudaMemcpyDeviceToDevice,
+                               c->stream));
+    copy_mat(c, m, r2, colmaj(U2.p, m), rowmaj(out->z2, r2));
+    // 11-12. new z3 = z3 P2^T with P2 = U2_r^T C2_left (r2 x R2)
+    DBuf<double> P2(c, (size_t)r2 * R2);
+    gemm(c, r2, R2, m, 1.0, trans(colmaj(U2.p, m)), rowmaj(C2.p, R2), 0.0, rowmaj(P2.p, R2));
+    gemm(c, n_x, r2, R2, 1.0, rowmaj(z->z3, R2), trans(rowmaj(P2.p, R2)), 0.0, rowmaj(out->z3, r2));
+    if (info) {
+        info->nrm_before = h.nrm;
+        info->nrm_after = h.nrm_after;
+    }
+    return out;
+}
+
+// ============================================================== inner products
+namespace {
+__global__ void k_frob_dot(int n, const double* __restrict__ a, const double* __restrict__ b,
+                           double* __restrict__ out) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s = fma(a[i], b[i], s);
+    __shared__ double red[32];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        s = warp_sum(s);
+        if (threadIdx.x == 0) *out = s;
+    }
+}
+}  // namespace
+
+void dot_dev(tt_ctx* c, const tt_t* a, const tt_t* b, double* dout) {
+    TT_REQUIRE(a->n_t == b->n_t && a->n_xi == b->n_xi && a->n_x == b->n_x, "dot: shape mismatch");
+    const int n_t = a->n_t, n_xi = a->n_xi, n_x = a->n_x;
+    const int ra1 = a->r1, ra2 = a->r2, rb1 = b->r1, rb2 = b->r2;
+    DBuf<double> W1(c, (size_t)ra1 * rb1);
+    gemm(c, ra1, rb1, n_t, 1.0, trans(colmaj(a->z1, n_t)), colmaj(b->z1, n_t), 0.0, rowmaj(W1.p, rb1));
+    DBuf<double> T(c, (size_t)ra1 * n_xi * rb2);
+    gemm(c, ra1, n_xi * rb2, rb1, 1.0, rowmaj(W1.p, rb1), rowmaj(b->z2, (long long)n_xi * rb2), 0.0,
+         rowmaj(T.p, (long long)n_xi * rb2));
+    DBuf<double> W2(c, (size_t)ra2 * rb2);
+    gemm(c, ra2, rb2, ra1 * n_xi, 1.0, trans(rowmaj(a->z2, ra2)), rowmaj(T.p, rb2), 0.0, rowmaj(W2.p, rb2));
+    DBuf<double> G3(c, (size_t)ra2 * rb2);
+    gemm(c, ra2, rb2, n_x, 1.0, trans(rowmaj(a->z3, ra2)), rowmaj(b->z3, rb2), 0.0, rowmaj(G3.p, rb2));
+    k_frob_dot<<<1, 256, 0, c->stream>>>(ra2 * rb2, W2.p, G3.p, dout);
+    LAUNCH_CHECK(c);
+}
+
+double dot_host(tt_ctx* c, const tt_t* a, const tt_t* b) {
+    DBuf<double> d(c, 1);
+    dot_dev(c, a, b, d.p);
+    double h;
+    read_back(c, d.p, &h, 1);
+    return h;
+}
+
+}  // namespace tt

@@ -1,0 +1,33 @@
+// Tensor-train operations of Section 4.1 on device-resident trains.
+#pragma once
+#include "la.cuh"
+
+namespace tt {
+
+// One summand of a concatenation: coef * (dcoef ? *dcoef : 1) * t.
+struct Summand {
+    double coef;
+    const double* dcoef;   // device scalar or nullptr
+    const tt_t* t;
+};
+
+// sum_i coef_i t_i by concatenating cores (ranks add).
+TTPtr concat(tt_ctx* c, const std::vector<Summand>& terms);
+
+// T_eps(z); fills the norms before / after truncation.
+struct RoundOut {
+    double nrm_before = 0.0, nrm_after = 0.0;
+};
+TTPtr round_tt(tt_ctx* c, const tt_t* z, double eps, RoundOut* info = nullptr);
+
+// <vec a, vec b> written to the device scalar *dout.
+void dot_dev(tt_ctx* c, const tt_t* a, const tt_t* b, double* dout);
+double dot_host(tt_ctx* c, const tt_t* a, const tt_t* b);
+
+// Copy of a train (same ranks), optionally scaled by a host scalar.
+TTPtr clone(tt_ctx* c, const tt_t* t, double scale = 1.0);
+
+// Rank-1 zero train.
+TTPtr zeros(tt_ctx* c, int n_t, int n_xi, int n_x);
+
+}  // namespace tt
