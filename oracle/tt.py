@@ -36,7 +36,10 @@ class TT:
 
     def full(self):
         """Dense n_t x n_xi x n_x array (eq. z_tt)."""
-        return np.einsum("ia,ajb,bk->ijk", self.z1, self.z2, self.z3)
+        n_t, n_xi, n_x = self.shape
+        k1, k2 = self.ranks
+        left = (self.z1 @ self.z2.reshape(k1, n_xi * k2)).reshape(n_t * n_xi, k2)
+        return (left @ self.z3).reshape(n_t, n_xi, n_x)
 
     def vec(self):
         return self.full().reshape(-1)
@@ -77,8 +80,9 @@ def add(*terms):
 def dot(x, y):
     """<vec x, vec y> by contracting the cores from the first to the last."""
     W = x.z1.T @ y.z1                                        # k1x x k1y
-    W = np.einsum("ab,asc,bsd->cd", W, x.z2, y.z2)           # k2x x k2y
-    return float(np.einsum("cd,ck,dk->", W, x.z3, y.z3))
+    T = np.einsum("ab,bsd->asd", W, y.z2)                    # k1x x n_xi x k2y
+    W = np.einsum("asc,asd->cd", x.z2, T)                    # k2x x k2y
+    return float(np.sum((W @ y.z3) * x.z3))
 
 
 def kron_apply(X1, X2, X3, z):
