@@ -185,6 +185,12 @@ typedef struct {
     double eps_conv;     /* truncation of the convection field, eq. (eps_conv) */
     double tol_inner;    /* inner (F_0 + C) solve stopping, Section 5.3 */
     int maxit_picard, maxit_gmres, maxit_inner;
+    int mixed;           /* 0: FP64 throughout; 1: inside GMRES (matvecs, truncations, the
+                            preconditioner) SpMM, GEMM, Householder R factors and banded
+                            solves compute in FP32 on FP64-stored trains, while inner
+                            products, Hessenberg least squares, the SVDs of the
+                            truncations, band factorisations, the Picard residual and the
+                            Picard-level truncations stay FP64 */
 } tt_solver_opts;
 
 typedef struct {

@@ -38,7 +38,7 @@ class ProblemDesc(C.Structure):
 class SolverOpts(C.Structure):
     _fields_ = [("tol_picard", _D), ("tol_gmres", _D), ("eps_gmres", _D), ("eps_soln", _D),
                 ("eps_conv", _D), ("tol_inner", _D), ("maxit_picard", _I), ("maxit_gmres", _I),
-                ("maxit_inner", _I)]
+                ("maxit_inner", _I), ("mixed", _I)]
 
 
 class GmresStats(C.Structure):

@@ -359,6 +359,7 @@ int tt_gmres(tt_ctx* ctx, tt_op* op, const tt_solver_opts* o, const tt_t* bu, co
     b.p = clone(ctx, bp);
     GmresOut go;
     tt_ctx* c = ctx;
+    PrecScope ps(ctx, o->mixed ? 1 : 0);
     Vec z = gmres(
         ctx, [c, op](const Vec& x) { Vec y; op_apply(c, op, x.u.get(), x.p.get(), &y.u, &y.p); return y; },
         [&pre](const Vec& v) { return pre.apply(v); }, b, o->tol_gmres, o->eps_gmres, o->maxit_gmres, bnorm, &go);

@@ -68,6 +68,10 @@ struct ProfData {
 struct tt_ctx {
     bool prof = false;
     ProfData pd;
+    // Compute precision of the SpMM, GEMM, Householder R factor and banded solves:
+    // 0 = FP64, 1 = FP32 arithmetic on FP64-stored data (the mixed path).  Jacobi
+    // SVDs, inner products, Hessenberg solves and band factorisations are FP64 always.
+    int fast = 0;
     cudaStream_t stream = nullptr;
     int device = 0;
     int nsm = 0;
@@ -152,6 +156,14 @@ struct ProfScope {
 };
 void prof_resolve(tt_ctx* c);
 
+// Sets the context's compute precision for its scope (restores on exit).
+struct PrecScope {
+    tt_ctx* c;
+    int saved;
+    PrecScope(tt_ctx* ctx, int fast) : c(ctx), saved(ctx->fast) { c->fast = fast; }
+    ~PrecScope() { c->fast = saved; }
+};
+
 }  // namespace tt
 
 // ---------------------------------------------------------------- tensor train
@@ -175,6 +187,11 @@ inline TTPtr wrap(tt_t* t) { return TTPtr(t, tt_free); }
 // ---------------------------------------------------------------- device helpers
 #ifdef __CUDACC__
 __device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;

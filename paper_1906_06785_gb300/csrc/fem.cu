@@ -172,6 +172,7 @@ __global__ void k_lp_band(int n_p, int bw, const int* __restrict__ brp, const in
 
 // ============================================================== sparse products
 namespace {
+template <typename TC>
 __global__ void __launch_bounds__(256)
 k_spmm_vel(VelSpmm s, const double* __restrict__ X, int ldx, double* __restrict__ Y, int ldy, int ncol) {
     const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -183,20 +184,20 @@ k_spmm_vel(VelSpmm s, const double* __restrict__ X, int ldx, double* __restrict_
     for (int b0 = 0; b0 < ncol; b0 += 32) {
         const int b = b0 + lane;
         const bool act = b < ncol;
-        double acc[8];
+        TC acc[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+        for (int q = 0; q < 8; ++q) acc[q] = TC(0);
         for (int k = k0; k < k1; ++k) {
             const int cl = s.col[k];
-            const double x = act ? Xc[(size_t)cl * ldx + b] : 0.0;
+            const TC x = act ? TC(Xc[(size_t)cl * ldx + b]) : TC(0);
 #pragma unroll
             for (int q = 0; q < 8; ++q)
-                if (q < s.nmat) acc[q] = fma(s.vals[q][k], x, acc[q]);
+                if (q < s.nmat) acc[q] = fma(TC(s.vals[q][k]), x, acc[q]);
         }
         if (act) {
 #pragma unroll
             for (int q = 0; q < 8; ++q)
-                if (q < s.nmat) Yr[s.coff[q] + b] = s.coef[q] * acc[q];
+                if (q < s.nmat) Yr[s.coff[q] + b] = s.coef[q] * (double)acc[q];
         }
     }
 }
@@ -244,7 +245,8 @@ void spmm_vel(tt_ctx* c, const VelSpmm& s, const double* X, int ldx, double* Y, 
     ProfScope prof(c, PROF_SPMM, 4.0 * nnz * ncol * s.nmat,
                    (double)nnz * (4 + 8 * s.nmat) + 4.0 * (s.n_rows + 1) + 8.0 * 2 * s.n_in * ncol +
                        8.0 * 2 * s.n_rows * ncol * s.nmat);
-    k_spmm_vel<<<ceil_div(threads, 256), 256, 0, c->stream>>>(s, X, ldx, Y, ldy, ncol);
+    (c->fast ? k_spmm_vel<float> : k_spmm_vel<double>)<<<ceil_div(threads, 256), 256, 0, c->stream>>>(
+        s, X, ldx, Y, ldy, ncol);
     LAUNCH_CHECK(c);
 }
 void spmm_div(tt_ctx* c, const Csr& B, const double* Bx, const double* By, int n_in, double coef,
@@ -291,34 +293,36 @@ __global__ void __launch_bounds__(1024) k_band_factor(double* __restrict__ ab, i
     }
 }
 
+template <typename TC>
 __global__ void k_band_solve(const double* __restrict__ ab, int n, int bw, double* __restrict__ X, int ldx,
                              int ncol, int ncomp) {
-    extern __shared__ double xs[];
+    extern __shared__ __align__(16) unsigned char xs_raw[];
+    TC* xs = reinterpret_cast<TC*>(xs_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int job = blockIdx.x * nw + warp;
     if (job >= ncol * ncomp) return;
     const int comp = job / ncol, b = job % ncol;
-    double* x = xs + (size_t)warp * n;
+    TC* x = xs + (size_t)warp * n;
     const int W = 2 * bw + 1;
-    for (int i = lane; i < n; i += 32) x[i] = X[((size_t)comp * n + i) * ldx + b];
+    for (int i = lane; i < n; i += 32) x[i] = TC(X[((size_t)comp * n + i) * ldx + b]);
     __syncwarp();
     for (int i = 0; i < n; ++i) {
         const int j0 = max(0, i - bw);
-        double s = 0.0;
-        for (int j = j0 + lane; j < i; j += 32) s = fma(ab[(size_t)i * W + j - i + bw], x[j], s);
+        TC s = TC(0);
+        for (int j = j0 + lane; j < i; j += 32) s = fma(TC(ab[(size_t)i * W + j - i + bw]), x[j], s);
         s = warp_sum(s);
         if (lane == 0) x[i] -= s;
         __syncwarp();
     }
     for (int i = n - 1; i >= 0; --i) {
         const int j1 = min(n - 1, i + bw);
-        double s = 0.0;
-        for (int j = i + 1 + lane; j <= j1; j += 32) s = fma(ab[(size_t)i * W + j - i + bw], x[j], s);
+        TC s = TC(0);
+        for (int j = i + 1 + lane; j <= j1; j += 32) s = fma(TC(ab[(size_t)i * W + j - i + bw]), x[j], s);
         s = warp_sum(s);
-        if (lane == 0) x[i] = (x[i] - s) / ab[(size_t)i * W + bw];
+        if (lane == 0) x[i] = (x[i] - s) / TC(ab[(size_t)i * W + bw]);
         __syncwarp();
     }
-    for (int i = lane; i < n; i += 32) X[((size_t)comp * n + i) * ldx + b] = x[i];
+    for (int i = lane; i < n; i += 32) X[((size_t)comp * n + i) * ldx + b] = (double)x[i];
 }
 }  // namespace
 
@@ -330,14 +334,15 @@ void band_factor(tt_ctx* c, double* ab, int n, int bw) {
 }
 
 void band_solve(tt_ctx* c, const double* ab, int n, int bw, double* X, int ldx, int ncol, int ncomp) {
-    const size_t per = (size_t)n * sizeof(double);
+    const size_t per = (size_t)n * (c->fast ? sizeof(float) : sizeof(double));
     int nw = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / per));
     const int jobs = ncol * ncomp;
     // forward + backward substitution: 2 * 2 n bw flops per column; band read once, columns in and out
     ProfScope prof(c, PROF_BAND_SOLVE, 4.0 * n * bw * jobs, 8.0 * n * (2 * bw + 1) + 16.0 * n * jobs);
     nw = std::min(nw, std::max(1, jobs));
-    CUDA_CHECK(cudaFuncSetAttribute(k_band_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    k_band_solve<<<ceil_div(jobs, nw), 32 * nw, per * nw, c->stream>>>(ab, n, bw, X, ldx, ncol, ncomp);
+    auto kern = c->fast ? k_band_solve<float> : k_band_solve<double>;
+    CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    kern<<<ceil_div(jobs, nw), 32 * nw, per * nw, c->stream>>>(ab, n, bw, X, ldx, ncol, ncomp);
     LAUNCH_CHECK(c);
 }
 

@@ -21,21 +21,22 @@ namespace tt {
 namespace {
 constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
 
+template <typename TC>
 __global__ void __launch_bounds__(256)
 k_gemm(int M, int N, int K, double alpha, const double* __restrict__ A, long long as0,
        long long as1, const double* __restrict__ B, long long bs0, long long bs1, double beta,
        double* __restrict__ C, long long cs0, long long cs1, int kchunk, double* __restrict__ part) {
-    __shared__ double As[GB_K][GB_M + 1];
-    __shared__ double Bs[GB_K][GB_N + 1];
+    __shared__ TC As[GB_K][GB_M + 1];
+    __shared__ TC Bs[GB_K][GB_N + 1];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int i0 = blockIdx.y * GB_M, j0 = blockIdx.x * GB_N;
     const int kbeg = blockIdx.z * kchunk;
     const int kend = min(K, kbeg + kchunk);
-    double acc[4][4];
+    TC acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+        for (int b = 0; b < 4; ++b) acc[a][b] = TC(0);
     const bool a_rowfast = (as1 == 1);   // k contiguous: iterate k fastest
     const bool b_colfast = (bs1 == 1);   // j contiguous: iterate j fastest
     for (int k0 = kbeg; k0 < kend; k0 += GB_K) {
@@ -43,18 +44,18 @@ k_gemm(int M, int N, int K, double alpha, const double* __restrict__ A, long lon
             int ii, kk;
             if (a_rowfast) { kk = e % GB_K; ii = e / GB_K; } else { ii = e % GB_M; kk = e / GB_M; }
             const int gi = i0 + ii, gk = k0 + kk;
-            As[kk][ii] = (gi < M && gk < kend) ? A[gi * as0 + gk * as1] : 0.0;
+            As[kk][ii] = (gi < M && gk < kend) ? TC(A[gi * as0 + gk * as1]) : TC(0);
         }
         for (int e = tid; e < GB_K * GB_N; e += 256) {
             int jj, kk;
             if (b_colfast) { jj = e % GB_N; kk = e / GB_N; } else { kk = e % GB_K; jj = e / GB_K; }
             const int gj = j0 + jj, gk = k0 + kk;
-            Bs[kk][jj] = (gj < N && gk < kend) ? B[gk * bs0 + gj * bs1] : 0.0;
+            Bs[kk][jj] = (gj < N && gk < kend) ? TC(B[gk * bs0 + gj * bs1]) : TC(0);
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < GB_K; ++kk) {
-            double av[4], bv[4];
+            TC av[4], bv[4];
 #pragma unroll
             for (int a = 0; a < 4; ++a) av[a] = As[kk][ty * 4 + a];
 #pragma unroll
@@ -74,11 +75,12 @@ k_gemm(int M, int N, int K, double alpha, const double* __restrict__ A, long lon
         for (int b = 0; b < 4; ++b) {
             const int gj = j0 + tx * 4 + b;
             if (gj >= N) continue;
+            const double v = (double)acc[a][b];
             if (part) {
-                part[((size_t)blockIdx.z * M + gi) * N + gj] = acc[a][b];
+                part[((size_t)blockIdx.z * M + gi) * N + gj] = v;
             } else {
                 double* cp = C + gi * cs0 + gj * cs1;
-                *cp = beta == 0.0 ? alpha * acc[a][b] : alpha * acc[a][b] + beta * *cp;
+                *cp = beta == 0.0 ? alpha * v : alpha * v + beta * *cp;
             }
         }
     }
@@ -120,14 +122,15 @@ void gemm(tt_ctx* c, int M, int N, int K, double alpha, MatView A, MatView B, do
     S = ceil_div(K, kchunk);
     dim3 grid(tn, tm, S);
     ProfScope prof(c, PROF_GEMM, 2.0 * M * N * K, 8.0 * ((double)M * K + (double)K * N + (double)M * N));
+    auto kern = c->fast ? k_gemm<float> : k_gemm<double>;
     if (S == 1) {
-        k_gemm<<<grid, 256, 0, c->stream>>>(M, N, K, alpha, A.p, A.s0, A.s1, B.p, B.s0, B.s1, beta,
-                                            C.p, C.s0, C.s1, kchunk, nullptr);
+        kern<<<grid, 256, 0, c->stream>>>(M, N, K, alpha, A.p, A.s0, A.s1, B.p, B.s0, B.s1, beta,
+                                          C.p, C.s0, C.s1, kchunk, nullptr);
         LAUNCH_CHECK(c);
     } else {
         DBuf<double> part(c, (size_t)S * M * N);
-        k_gemm<<<grid, 256, 0, c->stream>>>(M, N, K, alpha, A.p, A.s0, A.s1, B.p, B.s0, B.s1, beta,
-                                            C.p, C.s0, C.s1, kchunk, part.p);
+        kern<<<grid, 256, 0, c->stream>>>(M, N, K, alpha, A.p, A.s0, A.s1, B.p, B.s0, B.s1, beta,
+                                          C.p, C.s0, C.s1, kchunk, part.p);
         LAUNCH_CHECK(c);
         const long long tot = (long long)M * N;
         k_gemm_reduce<<<ceil_div(tot, 256), 256, 0, c->stream>>>(M, N, S, alpha, part.p, beta, C.p,
@@ -161,30 +164,32 @@ void fill_zero(tt_ctx* c, double* p, size_t n) {
 
 // ============================================================== QR (R only)
 namespace {
+template <typename TC>
 struct QRParams {
     int n, c, k, nb, nbp;
     const double* A;
     long long rs, cs;
     double* R;
     int ldr;
-    double* gwork;
-    double* part;    // [G]
-    double* part2;   // [G][c]
-    double* wv;      // [c]
-    double* diag;    // [1]
+    TC* gwork;
+    TC* part;    // [G]
+    TC* part2;   // [G][c]
+    TC* wv;      // [c]
+    TC* diag;    // [1]
     unsigned* bar;
     int* status;
 };
 
-__device__ double block_sum(double v, double* red) {
+template <typename TC>
+__device__ TC block_sum(TC v, TC* red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     v = warp_sum(v);
     __syncthreads();
     if (lane == 0) red[warp] = v;
     __syncthreads();
-    double s = 0.0;
+    TC s = TC(0);
     if (warp == 0) {
-        s = lane < nw ? red[lane] : 0.0;
+        s = lane < nw ? red[lane] : TC(0);
         s = warp_sum(s);
         if (lane == 0) red[0] = s;
     }
@@ -194,18 +199,21 @@ __device__ double block_sum(double v, double* red) {
     return s;
 }
 
-__global__ void __launch_bounds__(256) k_qr_r(QRParams P) {
-    extern __shared__ double sm[];
+// TC: arithmetic type (double, or float for the mixed path); input and R are FP64.
+template <typename TC>
+__global__ void __launch_bounds__(256) k_qr_r(QRParams<TC> P) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    TC* sm = reinterpret_cast<TC*>(sm_raw);
     const int g = blockIdx.x, G = gridDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int row0 = g * P.nb;
     const int rows = max(0, min(P.nb, P.n - row0));
-    double* v = sm;                 // [nbp]
-    double* red = sm + P.nbp;       // [32]
-    double* W = P.gwork ? P.gwork + (size_t)g * P.nbp * P.c : sm + P.nbp + 32;   // [c][nbp]
+    TC* v = sm;                     // [nbp]
+    TC* red = sm + P.nbp;           // [32]
+    TC* W = P.gwork ? P.gwork + (size_t)g * P.nbp * P.c : sm + P.nbp + 32;   // [c][nbp]
     for (int l = warp; l < P.c; l += nw)
         for (int i = lane; i < rows; i += 32)
-            W[(size_t)l * P.nbp + i] = P.A[(long long)(row0 + i) * P.rs + (long long)l * P.cs];
+            W[(size_t)l * P.nbp + i] = TC(P.A[(long long)(row0 + i) * P.rs + (long long)l * P.cs]);
     __syncthreads();
 
     for (int j = 0; j < P.k; ++j) {
@@ -213,9 +221,9 @@ __global__ void __launch_bounds__(256) k_qr_r(QRParams P) {
         const int jloc = j - row0;
         const bool own = (jloc >= 0 && jloc < rows);
         // A: partial sum of squares of column j strictly below row j, and the diagonal
-        double ss = 0.0;
+        TC ss = TC(0);
         for (int i = max(0, j + 1 - row0) + tid; i < rows; i += blockDim.x) {
-            const double x = W[(size_t)j * P.nbp + i];
+            const TC x = W[(size_t)j * P.nbp + i];
             ss += x * x;
         }
         ss = block_sum(ss, red);
@@ -226,33 +234,33 @@ __global__ void __launch_bounds__(256) k_qr_r(QRParams P) {
         grid_barrier(P.bar, G, P.status);
         // B: every CTA forms the same reflector (same data, same summation order)
         if (warp == 0) {
-            double s = 0.0;
+            TC s = TC(0);
             for (int q = lane; q < G; q += 32) s += __ldcg(P.part + q);
             s = warp_sum(s);
             if (lane == 0) { red[0] = s; red[1] = __ldcg(P.diag); }
         }
         __syncthreads();
-        const double sstail = red[0], x0 = red[1];
+        const TC sstail = red[0], x0 = red[1];
         __syncthreads();
-        if (sstail == 0.0) {      // reflector is the identity
+        if (sstail == TC(0)) {    // reflector is the identity
             if (own)
                 for (int l = tid; l < P.c; l += blockDim.x)
-                    P.R[(size_t)j * P.ldr + l] = l < j ? 0.0 : W[(size_t)l * P.nbp + jloc];
+                    P.R[(size_t)j * P.ldr + l] = l < j ? 0.0 : (double)W[(size_t)l * P.nbp + jloc];
             __syncthreads();
             continue;
         }
-        const double sigma = sqrt(x0 * x0 + sstail);
-        const double alpha = x0 >= 0.0 ? -sigma : sigma;
-        const double v0 = x0 - alpha;
-        const double beta = 2.0 / (v0 * v0 + sstail);
+        const TC sigma = sqrt(x0 * x0 + sstail);
+        const TC alpha = x0 >= TC(0) ? -sigma : sigma;
+        const TC v0 = x0 - alpha;
+        const TC beta = TC(2) / (v0 * v0 + sstail);
         for (int i = tid; i < rows; i += blockDim.x) {
             const int gi = row0 + i;
-            v[i] = gi < j ? 0.0 : (gi == j ? v0 : W[(size_t)j * P.nbp + i]);
+            v[i] = gi < j ? TC(0) : (gi == j ? v0 : W[(size_t)j * P.nbp + i]);
         }
         __syncthreads();
         const int ib = max(0, j - row0);
         for (int l = j + 1 + warp; l < P.c; l += nw) {
-            double p = 0.0;
+            TC p = TC(0);
             for (int i = ib + lane; i < rows; i += 32) p += v[i] * W[(size_t)l * P.nbp + i];
             p = warp_sum(p);
             if (lane == 0) P.part2[(size_t)g * P.c + l] = p;
@@ -261,7 +269,7 @@ __global__ void __launch_bounds__(256) k_qr_r(QRParams P) {
         // C: reduce-scatter of the reflector dots over all warps of the grid
         const int gw = g * nw + warp, TW = G * nw;
         for (int l = j + 1 + gw; l < P.c; l += TW) {
-            double s = 0.0;
+            TC s = TC(0);
             for (int q = lane; q < G; q += 32) s += __ldcg(P.part2 + (size_t)q * P.c + l);
             s = warp_sum(s);
             if (lane == 0) P.wv[l] = beta * s;
@@ -269,36 +277,36 @@ __global__ void __launch_bounds__(256) k_qr_r(QRParams P) {
         grid_barrier(P.bar, G, P.status);
         // D: apply the reflector to the trailing columns of the resident rows
         for (int l = j + 1 + warp; l < P.c; l += nw) {
-            const double wl = __ldcg(P.wv + l);
+            const TC wl = __ldcg(P.wv + l);
             for (int i = ib + lane; i < rows; i += 32) W[(size_t)l * P.nbp + i] -= v[i] * wl;
         }
         __syncthreads();
         if (own)
             for (int l = tid; l < P.c; l += blockDim.x)
-                P.R[(size_t)j * P.ldr + l] = l < j ? 0.0 : (l == j ? alpha : W[(size_t)l * P.nbp + jloc]);
+                P.R[(size_t)j * P.ldr + l] =
+                    l < j ? 0.0 : (double)(l == j ? alpha : W[(size_t)l * P.nbp + jloc]);
         __syncthreads();
     }
 }
-}  // namespace
 
-void qr_r(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr) {
-    TT_REQUIRE(n > 0 && cols > 0, "qr_r: empty matrix %d x %d", n, cols);
+template <typename TC>
+void qr_r_launch(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr) {
     const int k = std::min(n, cols);
     int G = std::min(c->nsm, std::max(1, ceil_div(n, 32)));
     const int nb = ceil_div(n, G);
     G = ceil_div(n, nb);
     const int nbp = nb | 1;
-    size_t smem = (size_t)(nbp + 32) * sizeof(double);
-    const size_t wbytes = (size_t)nbp * cols * sizeof(double);
-    DBuf<double> gwork;
+    size_t smem = (size_t)(nbp + 32) * sizeof(TC);
+    const size_t wbytes = (size_t)nbp * cols * sizeof(TC);
+    DBuf<TC> gwork;
     const size_t smem_limit = 200 * 1024;
     if (smem + wbytes <= smem_limit) {
         smem += wbytes;
     } else {
         gwork.alloc(c, (size_t)G * nbp * cols);
     }
-    DBuf<double> scratch(c, (size_t)G + (size_t)G * cols + cols + 1);
-    QRParams P;
+    DBuf<TC> scratch(c, (size_t)G + (size_t)G * cols + cols + 1);
+    QRParams<TC> P;
     P.n = n; P.c = cols; P.k = k; P.nb = nb; P.nbp = nbp;
     P.A = A.p; P.rs = A.s0; P.cs = A.s1;
     P.R = R; P.ldr = ldr;
@@ -310,14 +318,21 @@ void qr_r(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr) {
     P.bar = c->dbarrier;
     P.status = c->dstatus;
     CUDA_CHECK(cudaMemsetAsync(c->dbarrier, 0, 2 * sizeof(unsigned), c->stream));
-    CUDA_CHECK(cudaFuncSetAttribute(k_qr_r, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    CUDA_CHECK(cudaFuncSetAttribute(k_qr_r<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     // Householder R factor: 2 n c^2 - 2 c^3 / 3 flops (n >= c); reads A once, writes R
     const double kk = k;
-    ProfScope prof(c, PROF_QR, 2.0 * kk * kk * ((double)n + cols - kk) - 2.0 * kk * kk * kk / 3.0 + 0.0,
+    ProfScope prof(c, PROF_QR, 2.0 * kk * kk * ((double)n + cols - kk) - 2.0 * kk * kk * kk / 3.0,
                    8.0 * ((double)n * cols + kk * cols));
     void* args[] = {&P};
-    CUDA_CHECK(cudaLaunchCooperativeKernel((void*)k_qr_r, dim3(G), dim3(256), args, smem, c->stream));
+    CUDA_CHECK(cudaLaunchCooperativeKernel((void*)k_qr_r<TC>, dim3(G), dim3(256), args, smem, c->stream));
     count_launch(c);
+}
+}  // namespace
+
+void qr_r(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr) {
+    TT_REQUIRE(n > 0 && cols > 0, "qr_r: empty matrix %d x %d", n, cols);
+    if (c->fast) qr_r_launch<float>(c, n, cols, A, R, ldr);
+    else qr_r_launch<double>(c, n, cols, A, R, ldr);
 }
 
 // ============================================================== Jacobi SVD
@@ -444,6 +459,7 @@ static void jacobi_columns(tt_ctx* c, int m, int n, double* W, double* sig, doub
 
 void left_svd(tt_ctx* c, int m, int n, MatView A, double* sig, double* U) {
     TT_REQUIRE(m > 0 && n > 0, "left_svd: empty matrix");
+    PrecScope fp64(c, 0);   // the small SVDs of the truncation stay FP64, including their QR step
     if (n <= m) {
         DBuf<double> W(c, (size_t)m * n);
         copy_mat(c, m, n, A, colmaj(W.p, m));

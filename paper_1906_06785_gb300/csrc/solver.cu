@@ -232,8 +232,12 @@ void picard(tt_ctx* c, tt_problem* P, const tt_solver_opts* o, TTPtr* uo, TTPtr*
     op_init(c, &stokes, P, nullptr, TT_OP_FULL);
     LSCPrec pre{c, &stokes, o->eps_gmres, o->tol_inner, o->maxit_inner};
     GmresOut go;
-    Vec up = gmres(c, full_op(c, &stokes), [&pre](const Vec& v) { return pre.apply(v); }, f, o->tol_gmres,
+    Vec up;
+    {
+        PrecScope ps(c, o->mixed ? 1 : 0);
+        up = gmres(c, full_op(c, &stokes), [&pre](const Vec& v) { return pre.apply(v); }, f, o->tol_gmres,
                    o->eps_gmres, o->maxit_gmres, P->fnorm, &go);
+    }
     st->stokes_its = go.its;
     st->gmres_its[0] = go.its;
     st->inner_its[0] = pre.inner_its;
@@ -255,8 +259,12 @@ void picard(tt_ctx* c, tt_problem* P, const tt_solver_opts* o, TTPtr* uo, TTPtr*
         Vec r;
         r.u = std::move(ru);
         r.p = std::move(rp);
-        Vec d = gmres(c, full_op(c, &L), [&pr](const Vec& v) { return pr.apply(v); }, r, o->tol_gmres, o->eps_gmres,
-                      o->maxit_gmres, rn, &go);
+        Vec d;
+        {
+            PrecScope ps(c, o->mixed ? 1 : 0);
+            d = gmres(c, full_op(c, &L), [&pr](const Vec& v) { return pr.apply(v); }, r, o->tol_gmres,
+                      o->eps_gmres, o->maxit_gmres, rn, &go);
+        }
         st->gmres_its[i] = go.its;
         st->inner_its[i] = pr.inner_its;
         u = round_tt(c, concat(c, {Summand{1.0, nullptr, u.get()}, Summand{1.0, nullptr, d.u.get()}}).get(), o->eps_soln);

@@ -214,6 +214,7 @@ __global__ void k_frob_dot(int n, const double* __restrict__ a, const double* __
 
 void dot_dev(tt_ctx* c, const tt_t* a, const tt_t* b, double* dout) {
     TT_REQUIRE(a->n_t == b->n_t && a->n_xi == b->n_xi && a->n_x == b->n_x, "dot: shape mismatch");
+    PrecScope fp64(c, 0);   // inner products of the Arnoldi process stay FP64
     const int n_t = a->n_t, n_xi = a->n_xi, n_x = a->n_x;
     const int ra1 = a->r1, ra2 = a->r2, rb1 = b->r1, rb2 = b->r2;
     DBuf<double> W1(c, (size_t)ra1 * rb1);

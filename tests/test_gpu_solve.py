@@ -1,0 +1,118 @@
+"""GPU solves at workload sizes against the CPU oracle.
+
+* small workload: the full Picard solve (FP64 and mixed precision) against
+  samples of the oracle's solution stored by tests/golden/make_picard_golden.py;
+* medium workload (the benchmark's): one Kronecker matvec and one truncation of
+  medium-shaped trains, compared with the oracle on sampled entries and by TT
+  differences.
+
+Tolerances: FP64 path 1e-6 relative (sample error / largest sampled magnitude),
+mixed path 1e-4; matvec 1e-12 (same arithmetic, different summation order);
+truncation 1e-10 on inputs whose spectra keep every singular value away from
+the cut.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import tt as otm
+from oracle.system import Discretisation
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1906_06785_gb300 import binding
+    return binding.Context()
+
+
+def _golden(name):
+    path = os.path.join(GOLD, f"picard_{name}.txt")
+    g = {"u": [], "p": []}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, *v = line.split()
+        if k in ("u", "p"):
+            g[k].append((int(v[0]), int(v[1]), int(v[2]), float(v[3])))
+        elif k in ("picard_its", "stokes_its"):
+            g[k] = int(v[0])
+        elif k == "gmres_its":
+            g[k] = [int(x) for x in v]
+        elif k.startswith("ranks"):
+            g[k] = (int(v[0]), int(v[1]))
+        else:
+            g[k] = float(v[0])
+    return g
+
+
+def _sample_err(h, samples):
+    z1, z2, z3 = h.cores()
+    got = np.array([z1[i] @ z2[:, s, :] @ z3[:, j] for i, s, j, _ in samples])
+    ref = np.array([v for *_, v in samples])
+    return np.abs(got - ref).max() / np.abs(ref).max()
+
+
+@pytest.mark.parametrize("mixed,tol", [(0, 1e-6), (1, 1e-4)])
+def test_small_picard_matches_oracle(ctx, mixed, tol):
+    from paper_1906_06785_gb300 import binding
+    g = _golden("small")
+    prob = synth.preset("small")
+    P = ctx.problem(prob)
+    u, p, st, code = P.picard(binding.opts_from(prob.tol, mixed=mixed))
+    assert code == binding.TT_OK
+    assert st.res[st.picard_its] <= prob.tol.tol_picard * st.fnorm
+    assert _sample_err(u, g["u"]) < tol
+    assert _sample_err(p, g["p"]) < tol
+    if not mixed:
+        assert st.picard_its == g["picard_its"]
+
+
+def _medium_pair(ctx, d, seed):
+    u = otm.TT(*synth.random_tt(d.n_t, d.n_xi, d.n_u, 12, 30, seed=seed))
+    p = otm.TT(*synth.random_tt(d.n_t, d.n_xi, d.n_p, 10, 20, seed=seed + 1))
+    return u, p, ctx.tt(u.z1, u.z2, u.z3), ctx.tt(p.z1, p.z2, p.z3)
+
+
+@pytest.fixture(scope="module")
+def medium():
+    prob = synth.preset("medium")
+    return prob, Discretisation(prob)
+
+
+def test_medium_matvec_sampled(ctx, medium):
+    """L(w)[u;p] at the benchmark's sizes on 400 sampled entries (oracle evaluates
+    each entry from its own untruncated product)."""
+    prob, d = medium
+    P = ctx.problem(prob)
+    u, p, gu, gp = _medium_pair(ctx, d, 3)
+    w = d.full_velocity(otm.TT(*synth.random_tt(d.n_t, d.n_xi, d.n_u, 3, 6, seed=7)))
+    op = P.op(ctx.tt(w.z1, w.z2, w.z3))
+    ou, opp = op.matvec(gu, gp)
+    ru, rp = d.apply(w, u, p)
+    rng = np.random.default_rng(11)
+    for h, ref in ((ou, ru), (opp, rp)):
+        n_t, n_xi, n_x = ref.shape
+        samples = []
+        for _ in range(200):
+            i, s, j = int(rng.integers(n_t)), int(rng.integers(n_xi)), int(rng.integers(n_x))
+            samples.append((i, s, j, float(ref.z1[i] @ ref.z2[:, s, :] @ ref.z3[:, j])))
+        assert _sample_err(h, samples) < 1e-12
+
+
+def test_medium_round_tt_difference(ctx, medium):
+    """T_eps of a medium-shaped train with pre-truncation ranks like a matvec's."""
+    prob, d = medium
+    a = otm.TT(*synth.random_tt(d.n_t, d.n_xi, d.n_u, 40, 150, seed=21, decay=12))
+    b = otm.TT(*synth.random_tt(d.n_t, d.n_xi, d.n_u, 40, 150, seed=22, decay=12))
+    z = otm.add((1.0, a), (0.7, b))
+    g, nb, na = ctx.round(ctx.tt(z.z1, z.z2, z.z3), 1e-5)
+    ref, nref = otm.round_tt(z, 1e-5)
+    assert g.ranks == ref.ranks
+    og = otm.TT(*g.cores())
+    assert otm.norm(otm.add((1.0, og), (-1.0, ref))) / otm.norm(ref) < 1e-10
+    assert abs(nb - nref) < 1e-12 * nref
