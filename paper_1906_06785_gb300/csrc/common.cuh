@@ -72,6 +72,9 @@ struct tt_ctx {
     // 0 = FP64, 1 = FP32 arithmetic on FP64-stored data (the mixed path).  Jacobi
     // SVDs, inner products, Hessenberg solves and band factorisations are FP64 always.
     int fast = 0;
+    // Truncations with eps >= 5e-6 may take the Gram route (FP64 GEMMs and
+    // eigenpairs of small Gram matrices instead of Householder R factors).
+    bool gram_ok = true;
     cudaStream_t stream = nullptr;
     int device = 0;
     int nsm = 0;

@@ -12,6 +12,7 @@
 //    round-robin order, one warp per pair, one grid barrier per round.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "la.cuh"
 
@@ -100,6 +101,11 @@ __global__ void k_gemm_reduce(int M, int N, int S, double alpha, const double* _
 
 void gemm(tt_ctx* c, int M, int N, int K, double alpha, MatView A, MatView B, double beta,
           MatViewMut C) {
+    gemm_ws(c, M, N, K, alpha, A, B, beta, C, nullptr, 0);
+}
+
+void gemm_ws(tt_ctx* c, int M, int N, int K, double alpha, MatView A, MatView B, double beta,
+             MatViewMut C, double* ws, size_t ws_len) {
     if (M <= 0 || N <= 0) return;
     if (K <= 0) {
         // C = beta C
@@ -118,6 +124,8 @@ void gemm(tt_ctx* c, int M, int N, int K, double alpha, MatView A, MatView B, do
         S = std::min(ceil_div(target, tiles), ceil_div(K, 4 * GB_K));
         S = std::max(S, 1);
     }
+    // with a caller workspace, split-K is limited to what fits in it
+    if (ws && S > 1) S = std::max<long long>(1, std::min<long long>(S, (long long)(ws_len / ((size_t)M * N))));
     const int kchunk = ceil_div(ceil_div(K, S), GB_K) * GB_K;
     S = ceil_div(K, kchunk);
     dim3 grid(tn, tm, S);
@@ -128,12 +136,17 @@ void gemm(tt_ctx* c, int M, int N, int K, double alpha, MatView A, MatView B, do
                                           C.p, C.s0, C.s1, kchunk, nullptr);
         LAUNCH_CHECK(c);
     } else {
-        DBuf<double> part(c, (size_t)S * M * N);
+        DBuf<double> own;
+        double* part = ws;
+        if (!part) {
+            own.alloc(c, (size_t)S * M * N);
+            part = own.p;
+        }
         kern<<<grid, 256, 0, c->stream>>>(M, N, K, alpha, A.p, A.s0, A.s1, B.p, B.s0, B.s1, beta,
-                                          C.p, C.s0, C.s1, kchunk, part.p);
+                                          C.p, C.s0, C.s1, kchunk, part);
         LAUNCH_CHECK(c);
         const long long tot = (long long)M * N;
-        k_gemm_reduce<<<ceil_div(tot, 256), 256, 0, c->stream>>>(M, N, S, alpha, part.p, beta, C.p,
+        k_gemm_reduce<<<ceil_div(tot, 256), 256, 0, c->stream>>>(M, N, S, alpha, part, beta, C.p,
                                                                   C.s0, C.s1);
         LAUNCH_CHECK(c);
     }
@@ -166,16 +179,14 @@ void fill_zero(tt_ctx* c, double* p, size_t n) {
 namespace {
 template <typename TC>
 struct QRParams {
-    int n, c, k, nb, nbp;
+    int n, c, k, nb, nbp, L;
     const double* A;
     long long rs, cs;
     double* R;
     int ldr;
     TC* gwork;
-    TC* part;    // [G]
-    TC* part2;   // [G][c]
-    TC* wv;      // [c]
-    TC* diag;    // [1]
+    TC* part;    // [G][L] per-CTA partials of the combined reduction
+    TC* sums;    // [L]
     unsigned* bar;
     int* status;
 };
@@ -199,7 +210,35 @@ __device__ TC block_sum(TC v, TC* red) {
     return s;
 }
 
+// Per-CTA partials for column j over the resident rows i >= j:
+//   out[0]       = sum a_ij^2
+//   out[1 + l]   = sum a_ij a_il           (l > j)
+//   out[1 + c + l] = a_jl (owner of row j) (l >= j), 0 elsewhere
+template <typename TC>
+__device__ void qr_partials(const QRParams<TC>& P, const TC* W, int j, int row0, int rows, TC* red, TC* out) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int ib = max(0, j - row0);
+    const TC* wj = W + (size_t)j * P.nbp;
+    TC ss = TC(0);
+    for (int i = ib + tid; i < rows; i += blockDim.x) ss += wj[i] * wj[i];
+    ss = block_sum(ss, red);
+    if (tid == 0) out[0] = ss;
+    for (int l = j + 1 + warp; l < P.c; l += nw) {
+        const TC* wl = W + (size_t)l * P.nbp;
+        TC d = TC(0);
+        for (int i = ib + lane; i < rows; i += 32) d += wj[i] * wl[i];
+        d = warp_sum(d);
+        if (lane == 0) out[1 + l] = d;
+    }
+    const int jloc = j - row0;
+    const bool own = jloc >= 0 && jloc < rows;
+    for (int l = j + tid; l < P.c; l += blockDim.x) out[1 + P.c + l] = own ? W[(size_t)l * P.nbp + jloc] : TC(0);
+}
+
 // TC: arithmetic type (double, or float for the mixed path); input and R are FP64.
+// Householder with one combined reduction per column: v^T a_l = a_j^T a_l - alpha a_jl
+// lets the norm of column j, its products with the trailing columns and row j travel
+// together, so each column costs two grid barriers (partials ready, sums ready).
 template <typename TC>
 __global__ void __launch_bounds__(256) k_qr_r(QRParams<TC> P) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -208,95 +247,69 @@ __global__ void __launch_bounds__(256) k_qr_r(QRParams<TC> P) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int row0 = g * P.nb;
     const int rows = max(0, min(P.nb, P.n - row0));
-    TC* v = sm;                     // [nbp]
-    TC* red = sm + P.nbp;           // [32]
-    TC* W = P.gwork ? P.gwork + (size_t)g * P.nbp * P.c : sm + P.nbp + 32;   // [c][nbp]
+    TC* red = sm;                                   // [32]
+    TC* W = P.gwork ? P.gwork + (size_t)g * P.nbp * P.c : sm + 32;   // [c][nbp]
+    TC* mypart = P.part + (size_t)g * P.L;
     for (int l = warp; l < P.c; l += nw)
         for (int i = lane; i < rows; i += 32)
             W[(size_t)l * P.nbp + i] = TC(P.A[(long long)(row0 + i) * P.rs + (long long)l * P.cs]);
     __syncthreads();
-
+    if (P.k > 0) qr_partials(P, W, 0, row0, rows, red, mypart);
+    const int gw = g * nw + warp, TW = G * nw;
     for (int j = 0; j < P.k; ++j) {
         if (*(volatile int*)P.status != DEV_OK) return;
-        const int jloc = j - row0;
-        const bool own = (jloc >= 0 && jloc < rows);
-        // A: partial sum of squares of column j strictly below row j, and the diagonal
-        TC ss = TC(0);
-        for (int i = max(0, j + 1 - row0) + tid; i < rows; i += blockDim.x) {
-            const TC x = W[(size_t)j * P.nbp + i];
-            ss += x * x;
-        }
-        ss = block_sum(ss, red);
-        if (tid == 0) {
-            P.part[g] = ss;
-            if (own) P.diag[0] = W[(size_t)j * P.nbp + jloc];
+        grid_barrier(P.bar, G, P.status);
+        // reduce-scatter of the live entries: 0, 1 + (j, c), 1 + c + [j, c)
+        const int nd = P.c - j - 1, ne = P.c - j;
+        for (int t = gw; t < 1 + nd + ne; t += TW) {
+            const int idx = t == 0 ? 0 : (t <= nd ? 1 + j + t : 1 + P.c + j + (t - 1 - nd));
+            TC s = TC(0);
+            for (int q = lane; q < G; q += 32) s += __ldcg(P.part + (size_t)q * P.L + idx);
+            s = warp_sum(s);
+            if (lane == 0) P.sums[idx] = s;
         }
         grid_barrier(P.bar, G, P.status);
-        // B: every CTA forms the same reflector (same data, same summation order)
-        if (warp == 0) {
-            TC s = TC(0);
-            for (int q = lane; q < G; q += 32) s += __ldcg(P.part + q);
-            s = warp_sum(s);
-            if (lane == 0) { red[0] = s; red[1] = __ldcg(P.diag); }
-        }
-        __syncthreads();
-        const TC sstail = red[0], x0 = red[1];
-        __syncthreads();
-        if (sstail == TC(0)) {    // reflector is the identity
+        const TC ss = __ldcg(P.sums), x0 = __ldcg(P.sums + 1 + P.c + j);
+        const int jloc = j - row0;
+        const bool own = jloc >= 0 && jloc < rows;
+        if (ss == TC(0)) {      // zero column: R(j, :) is row j as it stands
             if (own)
                 for (int l = tid; l < P.c; l += blockDim.x)
                     P.R[(size_t)j * P.ldr + l] = l < j ? 0.0 : (double)W[(size_t)l * P.nbp + jloc];
-            __syncthreads();
-            continue;
-        }
-        const TC sigma = sqrt(x0 * x0 + sstail);
-        const TC alpha = x0 >= TC(0) ? -sigma : sigma;
-        const TC v0 = x0 - alpha;
-        const TC beta = TC(2) / (v0 * v0 + sstail);
-        for (int i = tid; i < rows; i += blockDim.x) {
-            const int gi = row0 + i;
-            v[i] = gi < j ? TC(0) : (gi == j ? v0 : W[(size_t)j * P.nbp + i]);
-        }
-        __syncthreads();
-        const int ib = max(0, j - row0);
-        for (int l = j + 1 + warp; l < P.c; l += nw) {
-            TC p = TC(0);
-            for (int i = ib + lane; i < rows; i += 32) p += v[i] * W[(size_t)l * P.nbp + i];
-            p = warp_sum(p);
-            if (lane == 0) P.part2[(size_t)g * P.c + l] = p;
-        }
-        grid_barrier(P.bar, G, P.status);
-        // C: reduce-scatter of the reflector dots over all warps of the grid
-        const int gw = g * nw + warp, TW = G * nw;
-        for (int l = j + 1 + gw; l < P.c; l += TW) {
-            TC s = TC(0);
-            for (int q = lane; q < G; q += 32) s += __ldcg(P.part2 + (size_t)q * P.c + l);
-            s = warp_sum(s);
-            if (lane == 0) P.wv[l] = beta * s;
-        }
-        grid_barrier(P.bar, G, P.status);
-        // D: apply the reflector to the trailing columns of the resident rows
-        for (int l = j + 1 + warp; l < P.c; l += nw) {
-            const TC wl = __ldcg(P.wv + l);
-            for (int i = ib + lane; i < rows; i += 32) W[(size_t)l * P.nbp + i] -= v[i] * wl;
+        } else {
+            const TC sigma = sqrt(ss);
+            const TC alpha = x0 >= TC(0) ? -sigma : sigma;
+            const TC v0 = x0 - alpha;
+            const TC beta = TC(1) / (ss + fabs(x0) * sigma);    // 2 / v^T v
+            const int ib = max(0, j - row0);
+            const TC* wj = W + (size_t)j * P.nbp;
+            for (int l = j + 1 + warp; l < P.c; l += nw) {
+                const TC el = __ldcg(P.sums + 1 + P.c + l);
+                const TC wl = beta * (__ldcg(P.sums + 1 + l) - alpha * el);
+                TC* col = W + (size_t)l * P.nbp;
+                for (int i = ib + lane; i < rows; i += 32) {
+                    const TC vi = (row0 + i == j) ? v0 : wj[i];
+                    col[i] -= vi * wl;
+                }
+                if (own && lane == 0) P.R[(size_t)j * P.ldr + l] = (double)(el - v0 * wl);
+            }
+            if (own)
+                for (int l = tid; l <= j; l += blockDim.x)
+                    P.R[(size_t)j * P.ldr + l] = l < j ? 0.0 : (double)alpha;
         }
         __syncthreads();
-        if (own)
-            for (int l = tid; l < P.c; l += blockDim.x)
-                P.R[(size_t)j * P.ldr + l] =
-                    l < j ? 0.0 : (double)(l == j ? alpha : W[(size_t)l * P.nbp + jloc]);
-        __syncthreads();
+        if (j + 1 < P.k) qr_partials(P, W, j + 1, row0, rows, red, mypart);
     }
 }
 
 template <typename TC>
 void qr_r_launch(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr) {
     const int k = std::min(n, cols);
-    int G = std::min(c->nsm, std::max(1, ceil_div(n, 32)));
+    int G = std::min(c->nsm, std::max(1, ceil_div(n, 16)));
     const int nb = ceil_div(n, G);
     G = ceil_div(n, nb);
     const int nbp = nb | 1;
-    size_t smem = (size_t)(nbp + 32) * sizeof(TC);
+    size_t smem = 32 * sizeof(TC);
     const size_t wbytes = (size_t)nbp * cols * sizeof(TC);
     DBuf<TC> gwork;
     const size_t smem_limit = 200 * 1024;
@@ -305,16 +318,15 @@ void qr_r_launch(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr) {
     } else {
         gwork.alloc(c, (size_t)G * nbp * cols);
     }
-    DBuf<TC> scratch(c, (size_t)G + (size_t)G * cols + cols + 1);
+    const int L = 2 * cols + 1;
+    DBuf<TC> scratch(c, (size_t)G * L + L);
     QRParams<TC> P;
-    P.n = n; P.c = cols; P.k = k; P.nb = nb; P.nbp = nbp;
+    P.n = n; P.c = cols; P.k = k; P.nb = nb; P.nbp = nbp; P.L = L;
     P.A = A.p; P.rs = A.s0; P.cs = A.s1;
     P.R = R; P.ldr = ldr;
     P.gwork = gwork.p;
     P.part = scratch.p;
-    P.part2 = scratch.p + G;
-    P.wv = scratch.p + G + (size_t)G * cols;
-    P.diag = P.wv + cols;
+    P.sums = scratch.p + (size_t)G * L;
     P.bar = c->dbarrier;
     P.status = c->dstatus;
     CUDA_CHECK(cudaMemsetAsync(c->dbarrier, 0, 2 * sizeof(unsigned), c->stream));
@@ -339,10 +351,13 @@ void qr_r(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr) {
 namespace {
 __global__ void __launch_bounds__(128)
 k_jacobi(int m, int n, int npad, double* W, int ldw, int* flags, int max_sweeps, double tol,
-         unsigned* bar, int* status, int* sweeps_used) {
+         unsigned* bar, int* status, int* sweeps_used, const double* frob2) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int gw = blockIdx.x * nw + warp, TW = gridDim.x * nw;
     const int P = npad / 2, NR = npad - 1;
+    // columns below 1e-15 ||A||_F are numerically zero: their pair products are noise
+    // and are not rotated (otherwise the sweep never meets the threshold)
+    const double tiny = 1e-30 * __ldcg(frob2);
     int sw = 0;
     for (; sw < max_sweeps; ++sw) {
         int any = 0;
@@ -359,7 +374,7 @@ k_jacobi(int m, int n, int npad, double* W, int ldw, int* flags, int max_sweeps,
                     al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
                 }
                 al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
-                if (al > 0.0 && be > 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+                if (al > tiny && be > tiny && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
                     const double zeta = (be - al) / (2.0 * ga);
                     const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                     const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
@@ -379,6 +394,20 @@ k_jacobi(int m, int n, int npad, double* W, int ldw, int* flags, int max_sweeps,
         if (*(volatile int*)status != DEV_OK) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_used = sw;
+}
+
+__global__ void k_frob2(long long len, const double* __restrict__ W, double* __restrict__ out) {
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < len; i += blockDim.x) s = fma(W[i], W[i], s);
+    __shared__ double red[32];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        s = warp_sum(s);
+        if (threadIdx.x == 0) *out = s;
+    }
 }
 
 __global__ void k_colnorms(int m, int n, const double* __restrict__ W, int ldw, double* __restrict__ nrm) {
@@ -412,19 +441,23 @@ __global__ void k_rank(int n, const double* __restrict__ nrm, int* __restrict__ 
     }
 }
 
+// Columns the Jacobi sweep treats as numerically zero (squared norm <= 1e-30 ||A||_F^2,
+// never rotated) get a zero left vector: normalising them would produce unit
+// vectors that are not orthogonal to the others.
 __global__ void k_permute_normalise(int m, int n, const double* __restrict__ W, int ldw,
                                     const double* __restrict__ nrm, const int* __restrict__ rank,
-                                    double* __restrict__ sig, double* __restrict__ U) {
+                                    double* __restrict__ sig, double* __restrict__ U,
+                                    const double* __restrict__ frob2) {
     const int col = blockIdx.x;
     const int dst = rank[col];
     const double s = nrm[col];
-    const double inv = s > 0.0 ? 1.0 / s : 0.0;
+    const double inv = (s > 0.0 && s * s > 1e-30 * *frob2) ? 1.0 / s : 0.0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) U[(size_t)dst * m + i] = W[(size_t)col * ldw + i] * inv;
     if (threadIdx.x == 0) sig[dst] = s;
 }
 }  // namespace
 
-static void jacobi_columns(tt_ctx* c, int m, int n, double* W, double* sig, double* U) {
+static void jacobi_columns(tt_ctx* c, int m, int n, double* W, double* sig, double* U, double ortho_tol) {
     // W: m x n column-major (ld m), overwritten by W V (orthogonal columns)
     const int npad = n + (n & 1);
     const int P = npad / 2;
@@ -434,18 +467,31 @@ static void jacobi_columns(tt_ctx* c, int m, int n, double* W, double* sig, doub
     DBuf<int> flags(c, max_sweeps + 1);
     CUDA_CHECK(cudaMemsetAsync(flags.p, 0, (max_sweeps + 1) * sizeof(int), c->stream));
     CUDA_CHECK(cudaMemsetAsync(c->dbarrier, 0, 2 * sizeof(unsigned), c->stream));
-    double tol = std::max(1e-15, std::sqrt((double)m) * 2.220446049250313e-16);
+    // Orthogonality target: FP64 dot products of nearly orthogonal columns carry
+    // rounding noise of order m eps_mach, so a tighter target only re-rotates noise;
+    // 1e-13 relative is far below any truncation tolerance used here.
+    double tol = std::max(ortho_tol, 4.0 * m * 2.220446049250313e-16);
     int* sweeps = flags.p + max_sweeps;
+    DBuf<double> frob2(c, 1);
+    k_frob2<<<1, 256, 0, c->stream>>>((long long)m * n, W, frob2.p);
+    LAUNCH_CHECK(c);
     int mm = m, nn = n, np_ = npad, ld = m, ms = max_sweeps;
     unsigned* bar = c->dbarrier;
     int* st = c->dstatus;
     int* fl = flags.p;
-    void* args[] = {&mm, &nn, &np_, &W, &ld, &fl, &ms, &tol, &bar, &st, &sweeps};
+    double* f2 = frob2.p;
+    void* args[] = {&mm, &nn, &np_, &W, &ld, &fl, &ms, &tol, &bar, &st, &sweeps, &f2};
     if (n > 1) {
         // one sweep: n(n-1)/2 pairs x (3 dots + 1 rotation) over m rows = 12 m flops per pair
         ProfScope prof(c, PROF_JACOBI, 6.0 * n * (n - 1.0) * m, 16.0 * (double)m * n);
         CUDA_CHECK(cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(G), dim3(32 * wpb), args, 0, c->stream));
         count_launch(c);
+        static const bool log = getenv("TT_LOG_ROUND") != nullptr;
+        if (log) {
+            int sw = 0;
+            read_back(c, (const int*)sweeps, &sw, 1);
+            fprintf(stderr, "jacobi m=%d n=%d sweeps=%d\n", m, n, sw);
+        }
     }
     DBuf<double> nrm(c, n);
     DBuf<int> rank(c, n);
@@ -453,17 +499,19 @@ static void jacobi_columns(tt_ctx* c, int m, int n, double* W, double* sig, doub
     LAUNCH_CHECK(c);
     k_rank<<<ceil_div(n, 256), 256, 0, c->stream>>>(n, nrm.p, rank.p);
     LAUNCH_CHECK(c);
-    k_permute_normalise<<<n, 256, 0, c->stream>>>(m, n, W, m, nrm.p, rank.p, sig, U);
+    k_permute_normalise<<<n, 256, 0, c->stream>>>(m, n, W, m, nrm.p, rank.p, sig, U, frob2.p);
     LAUNCH_CHECK(c);
 }
 
-void left_svd(tt_ctx* c, int m, int n, MatView A, double* sig, double* U) {
+void left_svd(tt_ctx* c, int m, int n, MatView A, double* sig, double* U, double ortho_tol) {
     TT_REQUIRE(m > 0 && n > 0, "left_svd: empty matrix");
-    PrecScope fp64(c, 0);   // the small SVDs of the truncation stay FP64, including their QR step
+    // The SVD proper (Jacobi) is FP64 always.  When n > m the m x n matrix is first
+    // reduced to an m x m triangle by an R factor, which follows the context's
+    // precision (FP32 on the mixed path).
     if (n <= m) {
         DBuf<double> W(c, (size_t)m * n);
         copy_mat(c, m, n, A, colmaj(W.p, m));
-        jacobi_columns(c, m, n, W.p, sig, U);
+        jacobi_columns(c, m, n, W.p, sig, U, ortho_tol);
     } else {
         // A = R^T Q^T with A^T = Q R: left singular vectors of A are those of R^T (m x m)
         DBuf<double> R(c, (size_t)m * m);
@@ -472,7 +520,7 @@ void left_svd(tt_ctx* c, int m, int n, MatView A, double* sig, double* U) {
         // W = R^T column-major: W(i, j) = R(j, i) -> element (i,j) at j*m + i = R[j*m + i]
         CUDA_CHECK(cudaMemcpyAsync(W.p, R.p, (size_t)m * m * sizeof(double), cudaMemcpyDeviceToDevice,
                                    c->stream));
-        jacobi_columns(c, m, m, W.p, sig, U);
+        jacobi_columns(c, m, m, W.p, sig, U, ortho_tol);
     }
 }
 

@@ -25,6 +25,10 @@ inline MatViewMut colmaj(double* p, long long ld) { return {p, 1, ld}; }
 // C (M x N) = alpha A (M x K) B (K x N) + beta C.  beta == 0 never reads C.
 void gemm(tt_ctx* c, int M, int N, int K, double alpha, MatView A, MatView B, double beta,
           MatViewMut C);
+// Same, with split-K partial sums in a caller workspace of ws_len doubles (no
+// allocation; split-K shrinks to what fits, down to none).
+void gemm_ws(tt_ctx* c, int M, int N, int K, double alpha, MatView A, MatView B, double beta,
+             MatViewMut C, double* ws, size_t ws_len);
 
 // R factor (k x c upper trapezoidal, k = min(n, c), row-major with leading
 // dimension ldr) of the n x c matrix A by Householder QR.  Q is not formed.
@@ -33,7 +37,10 @@ void qr_r(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr);
 // Left singular vectors and singular values of the m x n matrix A (any strides).
 // Writes sig (p = min(m, n) values, descending) and U (m x p, column-major,
 // ld m; column i belongs to sig[i]; columns of zero singular values are zero).
-void left_svd(tt_ctx* c, int m, int n, MatView A, double* sig, double* U);
+// ortho_tol: Jacobi stops when every column pair has |a.b| <= ortho_tol |a||b|
+// (at least 4 m eps_mach); singular values then carry absolute errors of order
+// ortho_tol * sigma_max.
+void left_svd(tt_ctx* c, int m, int n, MatView A, double* sig, double* U, double ortho_tol = 1e-13);
 
 // Truncation of Section 4.1 on device data: given sorted sig1 (p1) and sig2 (p2)
 // it is applied in two calls; see trunc.cu.

@@ -11,6 +11,7 @@
 // exact arithmetic this is the same T_eps, and it needs no orthogonal factor Q.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "tt.cuh"
 
@@ -128,26 +129,166 @@ TTPtr concat(tt_ctx* c, const std::vector<Summand>& terms) {
 }
 
 // ============================================================== truncation
-TTPtr round_tt(tt_ctx* c, const tt_t* z, double eps, RoundOut* info) {
+namespace {
+__global__ void k_sqrt_abs(int n, double* __restrict__ v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = sqrt(fabs(v[i]));
+}
+}  // namespace
+
+// Truncation through Gram matrices, for tolerances well above sqrt(machine eps):
+// the singular values and left singular vectors of both unfoldings are the
+// eigenpairs of S1 = Z(1) Z(1)^T (n_t x n_t) and, after projecting mode 1, of
+// S2 = Z(2) Z(2)^T ((r1 n_xi) x (r1 n_xi)), assembled from the cores by FP64 GEMMs
+// (no QR).  One-sided Jacobi on a symmetric PSD matrix returns its eigenvectors
+// with column norms equal to the eigenvalues.  Eigenvalues carry an absolute
+// error of order n eps_mach ||z||^2, far below delta^2 = eps^2 ||z||^2 / 2 here.
+static TTPtr round_gram(tt_ctx* c, const tt_t* z, double eps, RoundOut* info) {
+    PrecScope fp64(c, 0);
     const int n_t = z->n_t, n_xi = z->n_xi, n_x = z->n_x, R1 = z->r1, R2 = z->r2;
-    // 1. R3: R factor of z3 (n_x x R2, row-major)
-    const int k = std::min(n_x, R2);
-    DBuf<double> R3(c, (size_t)k * R2);
-    qr_r(c, n_x, R2, rowmaj(z->z3, R2), R3.p, R2);
+    // G3 = z3^T z3 costs 2 R2^2 (n_x + R1 n_xi) flops, X = z2_left z3^T costs 2 R1 n_xi R2 n_x
+    const bool wide = (double)R2 * (n_x + (double)R1 * n_xi) >= (double)R1 * n_xi * n_x;
+    // W2 = sum_s (z2_s F^T)(z2_s F^T)^T with F^T F = z3 z3^T-metric:
+    //   narrow: G3 = z3^T z3 (R2 x R2), T = z2_left G3, W2 = z2_r T_r^T
+    //   wide:   X = z2_left z3^T ((R1 n_xi) x n_x), W2 = X_r X_r^T
+    DBuf<double> G3, X, W2(c, (size_t)R1 * R1);
+    if (!wide) {
+        G3.alloc(c, (size_t)R2 * R2);
+        gemm(c, R2, R2, n_x, 1.0, trans(rowmaj(z->z3, R2)), rowmaj(z->z3, R2), 0.0, rowmaj(G3.p, R2));
+        DBuf<double> T(c, (size_t)R1 * n_xi * R2);
+        gemm(c, R1 * n_xi, R2, R2, 1.0, rowmaj(z->z2, R2), rowmaj(G3.p, R2), 0.0, rowmaj(T.p, R2));
+        gemm(c, R1, R1, n_xi * R2, 1.0, rowmaj(z->z2, (long long)n_xi * R2), trans(rowmaj(T.p, (long long)n_xi * R2)),
+             0.0, rowmaj(W2.p, R1));
+    } else {
+        X.alloc(c, (size_t)R1 * n_xi * n_x);
+        gemm(c, R1 * n_xi, n_x, R2, 1.0, rowmaj(z->z2, R2), trans(rowmaj(z->z3, R2)), 0.0, rowmaj(X.p, n_x));
+        gemm(c, R1, R1, n_xi * n_x, 1.0, rowmaj(X.p, (long long)n_xi * n_x), trans(rowmaj(X.p, (long long)n_xi * n_x)),
+             0.0, rowmaj(W2.p, R1));
+    }
+    // S1 = z1 W2 z1^T
+    DBuf<double> tmp(c, (size_t)n_t * R1), S1(c, (size_t)n_t * n_t);
+    gemm(c, n_t, R1, R1, 1.0, colmaj(z->z1, n_t), rowmaj(W2.p, R1), 0.0, colmaj(tmp.p, n_t));
+    gemm(c, n_t, n_t, R1, 1.0, colmaj(tmp.p, n_t), trans(colmaj(z->z1, n_t)), 0.0, colmaj(S1.p, n_t));
+    DBuf<double> sig1(c, n_t), U1(c, (size_t)n_t * n_t);
+    left_svd(c, n_t, n_t, colmaj(S1.p, n_t), sig1.p, U1.p);
+    k_sqrt_abs<<<ceil_div(n_t, 256), 256, 0, c->stream>>>(n_t, sig1.p);
+    LAUNCH_CHECK(c);
+    DBuf<TruncInfo> dinfo(c, 1);
+    trunc_first(c, sig1.p, n_t, eps, dinfo.p);
+    TruncInfo h;
+    read_back(c, dinfo.p, &h, 1);
+    check_status(c);
+    if (!(h.nrm == h.nrm) || std::isinf(h.nrm)) TT_THROW(TT_ENAN, "non-finite norm in truncation");
+    if (h.nrm == 0.0) {
+        if (info) { info->nrm_before = 0.0; info->nrm_after = 0.0; }
+        return zeros(c, n_t, n_xi, n_x);
+    }
+    const int r1 = h.r1;
+    DBuf<double> P1(c, (size_t)r1 * R1);
+    gemm(c, r1, R1, n_t, 1.0, trans(colmaj(U1.p, n_t)), colmaj(z->z1, n_t), 0.0, rowmaj(P1.p, R1));
+    DBuf<double> C2(c, (size_t)r1 * n_xi * R2);
+    gemm(c, r1, n_xi * R2, R1, 1.0, rowmaj(P1.p, R1), rowmaj(z->z2, (long long)n_xi * R2), 0.0,
+         rowmaj(C2.p, (long long)n_xi * R2));
+    const int m = r1 * n_xi;
+    // S2 = C2_left G3 C2_left^T (narrow) or (C2_left z3^T)(C2_left z3^T)^T (wide)
+    DBuf<double> S2(c, (size_t)m * m);
+    if (!wide) {
+        DBuf<double> T2(c, (size_t)m * R2);
+        gemm(c, m, R2, R2, 1.0, rowmaj(C2.p, R2), rowmaj(G3.p, R2), 0.0, rowmaj(T2.p, R2));
+        gemm(c, m, m, R2, 1.0, rowmaj(T2.p, R2), trans(rowmaj(C2.p, R2)), 0.0, colmaj(S2.p, m));
+    } else {
+        DBuf<double> Y(c, (size_t)m * n_x);
+        gemm(c, m, n_x, R2, 1.0, rowmaj(C2.p, R2), trans(rowmaj(z->z3, R2)), 0.0, rowmaj(Y.p, n_x));
+        gemm(c, m, m, n_x, 1.0, rowmaj(Y.p, n_x), trans(rowmaj(Y.p, n_x)), 0.0, colmaj(S2.p, m));
+    }
+    DBuf<double> sig2(c, m), U2(c, (size_t)m * m);
+    left_svd(c, m, m, colmaj(S2.p, m), sig2.p, U2.p);
+    k_sqrt_abs<<<ceil_div(m, 256), 256, 0, c->stream>>>(m, sig2.p);
+    LAUNCH_CHECK(c);
+    trunc_second(c, sig2.p, m, eps, dinfo.p);
+    read_back(c, dinfo.p, &h, 1);
+    check_status(c);
+    const int r2 = h.r2;
+    TTPtr out = wrap(tt_alloc(c, n_t, n_xi, n_x, r1, r2));
+    CUDA_CHECK(cudaMemcpyAsync(out->z1, U1.p, (size_t)n_t * r1 * sizeof(double), cudaMemcpyDeviceToDevice,
+                               c->stream));
+    copy_mat(c, m, r2, colmaj(U2.p, m), rowmaj(out->z2, r2));
+    DBuf<double> P2(c, (size_t)r2 * R2);
+    gemm(c, r2, R2, m, 1.0, trans(colmaj(U2.p, m)), rowmaj(C2.p, R2), 0.0, rowmaj(P2.p, R2));
+    gemm(c, n_x, r2, R2, 1.0, rowmaj(z->z3, R2), trans(rowmaj(P2.p, R2)), 0.0, rowmaj(out->z3, r2));
+    if (info) {
+        info->nrm_before = h.nrm;
+        info->nrm_after = h.nrm_after;
+    }
+    static const bool log = getenv("TT_LOG_ROUND") != nullptr;
+    if (log)
+        fprintf(stderr, "round-gram n=(%d,%d,%d) R=(%d,%d) -> (%d,%d) eps=%.1e\n", n_t, n_xi, n_x, R1, R2, r1, r2,
+                eps);
+    return out;
+}
+
+// When the first rank exceeds n_t, replace z1 by an orthonormal basis U0 of its
+// column space (left singular vectors, FP64) and absorb U0^T z1 into the middle
+// core: the same tensor with first rank <= n_t, so every later product and factor
+// of the truncation works on n_t instead of R1 rows of the middle core.
+TTPtr round_tt(tt_ctx* c, const tt_t* z, double eps, RoundOut* info) {
+    if (z->r1 > z->n_t) {
+        const int n_t = z->n_t, n_xi = z->n_xi, R1 = z->r1, R2 = z->r2;
+        DBuf<double> sig(c, n_t), U0(c, (size_t)n_t * n_t);
+        {
+            PrecScope fp64(c, 0);
+            left_svd(c, n_t, R1, colmaj(z->z1, n_t), sig.p, U0.p);
+        }
+        DBuf<double> F1(c, (size_t)n_t * R1), z2c(c, (size_t)n_t * n_xi * R2);
+        gemm(c, n_t, R1, n_t, 1.0, trans(colmaj(U0.p, n_t)), colmaj(z->z1, n_t), 0.0, rowmaj(F1.p, R1));
+        gemm(c, n_t, n_xi * R2, R1, 1.0, rowmaj(F1.p, R1), rowmaj(z->z2, (long long)n_xi * R2), 0.0,
+             rowmaj(z2c.p, (long long)n_xi * R2));
+        tt_t view = *z;     // non-owning view: compressed cores 1, 2 and the original core 3
+        view.base = nullptr;
+        view.r1 = n_t;
+        view.z1 = U0.p;
+        view.z2 = z2c.p;
+        return round_tt(c, &view, eps, info);
+    }
+    // plain FP64 path: Gram route for tolerances well above sqrt(eps_mach); the mixed
+    // path keeps the R-factor route, whose products it runs in FP32
+    if (eps >= kGramMinEps && c->gram_ok && !c->fast) return round_gram(c, z, eps, info);
+    const int n_t = z->n_t, n_xi = z->n_xi, n_x = z->n_x, R1 = z->r1, R2 = z->r2;
+    // 1. R3 with z3 = Q3 R3 (z3: n_x x R2 row-major, Q3 orthonormal columns).  Q3 = I
+    //    with R3 = z3 is always a valid choice; a Householder R factor (k = R2 rows)
+    //    pays off only when R2 is well below n_x, since its columns are sequential.
+    const bool use_qr = 4 * R2 < n_x;
+    const int k = use_qr ? R2 : n_x;
+    DBuf<double> R3buf;
+    const double* R3 = z->z3;
+    if (use_qr) {
+        R3buf.alloc(c, (size_t)k * R2);
+        qr_r(c, n_x, R2, rowmaj(z->z3, R2), R3buf.p, R2);
+        R3 = R3buf.p;
+    }
     // 2. Y2 = z2 x3 R3 : (R1 n_xi x R2) (R2 x k)
     DBuf<double> Y2(c, (size_t)R1 * n_xi * k);
-    gemm(c, R1 * n_xi, k, R2, 1.0, rowmaj(z->z2, R2), trans(rowmaj(R3.p, R2)), 0.0, rowmaj(Y2.p, k));
-    // 3. Rf2: R factor of (right unfolding of Y2)^T, an (n_xi k) x R1 matrix
+    gemm(c, R1 * n_xi, k, R2, 1.0, rowmaj(z->z2, R2), trans(rowmaj(R3, R2)), 0.0, rowmaj(Y2.p, k));
+    // 3. Rf2 with M2 = Q2 Rf2, M2 = (right unfolding of Y2)^T, an (n_xi k) x R1 matrix;
+    //    again M2 itself when R1 >= n_xi k.  Rf2 is k1 x R1, read through (s0, s1).
     const int k1 = std::min(n_xi * k, R1);
-    DBuf<double> Rf2(c, (size_t)k1 * R1);
-    qr_r(c, n_xi * k, R1, MatView{Y2.p, 1, (long long)n_xi * k}, Rf2.p, R1);
+    DBuf<double> Rf2buf;
+    MatView Rf2{Y2.p, 1, (long long)n_xi * k};
+    if (R1 < n_xi * k) {
+        Rf2buf.alloc(c, (size_t)k1 * R1);
+        qr_r(c, n_xi * k, R1, MatView{Y2.p, 1, (long long)n_xi * k}, Rf2buf.p, R1);
+        Rf2 = rowmaj((const double*)Rf2buf.p, R1);
+    }
     // 4. A1 = z1 Rf2^T (n_t x k1): same singular values / left vectors as the first unfolding
     DBuf<double> A1(c, (size_t)n_t * k1);
-    gemm(c, n_t, k1, R1, 1.0, colmaj(z->z1, n_t), trans(rowmaj(Rf2.p, R1)), 0.0, colmaj(A1.p, n_t));
+    gemm(c, n_t, k1, R1, 1.0, colmaj(z->z1, n_t), trans(Rf2), 0.0, colmaj(A1.p, n_t));
     // 5. left SVD, ||z||, delta, r1
     const int p1 = std::min(n_t, k1);
     DBuf<double> sig1(c, p1), U1(c, (size_t)n_t * p1);
-    left_svd(c, n_t, k1, colmaj(A1.p, n_t), sig1.p, U1.p);
+    // Jacobi target matched to the truncation: columns orthogonal to 1e-3 eps leave
+    // singular-value errors of order 1e-3 eps sigma_max, far from the cut at eps ||z||
+    const double jtol = eps > 0.0 ? std::min(1e-8, std::max(1e-13, 1e-3 * eps)) : 1e-13;
+    left_svd(c, n_t, k1, colmaj(A1.p, n_t), sig1.p, U1.p, jtol);
     DBuf<TruncInfo> dinfo(c, 1);
     trunc_first(c, sig1.p, p1, eps, dinfo.p);
     TruncInfo h;
@@ -169,11 +310,11 @@ TTPtr round_tt(tt_ctx* c, const tt_t* z, double eps, RoundOut* info) {
     // 8. Y = C2_left R3^T (m x k), m = r1 n_xi
     const int m = r1 * n_xi;
     DBuf<double> Y(c, (size_t)m * k);
-    gemm(c, m, k, R2, 1.0, rowmaj(C2.p, R2), trans(rowmaj(R3.p, R2)), 0.0, colmaj(Y.p, m));
+    gemm(c, m, k, R2, 1.0, rowmaj(C2.p, R2), trans(rowmaj(R3, R2)), 0.0, colmaj(Y.p, m));
     // 9. left SVD of Y, r2
     const int p2 = std::min(m, k);
     DBuf<double> sig2(c, p2), U2(c, (size_t)m * p2);
-    left_svd(c, m, k, colmaj(Y.p, m), sig2.p, U2.p);
+    left_svd(c, m, k, colmaj(Y.p, m), sig2.p, U2.p, jtol);
     trunc_second(c, sig2.p, p2, eps, dinfo.p);
     read_back(c, dinfo.p, &h, 1);
     check_status(c);
@@ -191,6 +332,10 @@ TTPtr round_tt(tt_ctx* c, const tt_t* z, double eps, RoundOut* info) {
         info->nrm_before = h.nrm;
         info->nrm_after = h.nrm_after;
     }
+    static const bool log = getenv("TT_LOG_ROUND") != nullptr;
+    if (log)
+        fprintf(stderr, "round n=(%d,%d,%d) R=(%d,%d) -> (%d,%d) eps=%.1e fast=%d\n", n_t, n_xi, n_x, R1, R2, r1,
+                r2, eps, c->fast);
     return out;
 }
 

@@ -14,6 +14,9 @@ struct Summand {
 // sum_i coef_i t_i by concatenating cores (ranks add).
 TTPtr concat(tt_ctx* c, const std::vector<Summand>& terms);
 
+// Truncations with eps at or above this use the Gram route (see tt.cu).
+constexpr double kGramMinEps = 5e-6;
+
 // T_eps(z); fills the norms before / after truncation.
 struct RoundOut {
     double nrm_before = 0.0, nrm_after = 0.0;

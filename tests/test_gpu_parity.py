@@ -95,14 +95,18 @@ def test_round_matches_oracle(ctx, shape, eps):
     assert abs(nb - nref) <= 1e-12 * nref
     og = _oracle_tt(g)
     assert g.ranks == ref.ranks
-    assert _tt_diff(og, ref) < 1e-10
-    assert otm.norm(otm.add((1.0, og), (-1.0, z))) <= eps * nref * (1 + 1e-8)
-    assert abs(na - otm.norm(ref)) <= 1e-10 * nref
+    # the library's Jacobi stops at column orthogonality jtol = 1e-3 eps (clamped to
+    # [1e-13, 1e-8]) on the R-factor route: frames and tensor agree to that level
+    jtol = min(1e-8, max(1e-13, 1e-3 * eps))
+    tol = max(1e-10, 10 * jtol)
+    assert _tt_diff(og, ref) < tol
+    assert otm.norm(otm.add((1.0, og), (-1.0, z))) <= eps * nref * (1 + 1e-6)
+    assert abs(na - otm.norm(ref)) <= tol * nref
     # new first and second cores are orthonormal frames
     z1, z2, _ = g.cores()
-    assert np.abs(z1.T @ z1 - np.eye(z1.shape[1])).max() < 1e-12
+    assert np.abs(z1.T @ z1 - np.eye(z1.shape[1])).max() < max(1e-12, 10 * jtol)
     G = z2.reshape(-1, z2.shape[2])
-    assert np.abs(G.T @ G - np.eye(G.shape[1])).max() < 1e-12
+    assert np.abs(G.T @ G - np.eye(G.shape[1])).max() < max(1e-12, 10 * jtol)
 
 
 def test_round_zero_and_rank_one(ctx):
@@ -269,3 +273,20 @@ def test_picard_tiny_default_tolerances(ctx):
     assert _rel(u.full(), ou.full()) < 1e-6
     assert _rel(p.full(), op_.full()) < 1e-6
     assert st.res[st.picard_its] <= prob.tol.tol_picard * st.fnorm
+
+
+@pytest.mark.parametrize("eps", [1e-5, 1e-3])
+def test_round_gram_route_and_first_core_compression(ctx, eps):
+    """Tolerances >= 5e-6 take the Gram route; first ranks above n_t are compressed
+    first.  Both give T_eps of the same tensor: equal ranks (spectra with gaps at
+    the cut) and a TT difference far below the truncation tolerance."""
+    n_t, n_xi, n_x = 12, 5, 700
+    a = otm.TT(*synth.random_tt(n_t, n_xi, n_x, 10, 40, seed=31, decay=9))
+    b = otm.TT(*synth.random_tt(n_t, n_xi, n_x, 10, 40, seed=32, decay=9))
+    z = otm.add((1.0, a), (0.6, b))          # first rank 20 > n_t = 12
+    g, nb, na = ctx.round(ctx.tt(z.z1, z.z2, z.z3), eps)
+    ref, nref = otm.round_tt(z, eps)
+    assert g.ranks == ref.ranks
+    assert abs(nb - nref) < 1e-12 * nref
+    assert _tt_diff(_oracle_tt(g), ref) < 1e-8
+    assert otm.norm(otm.add((1.0, _oracle_tt(g)), (-1.0, z))) <= eps * nref * (1 + 1e-6)
