@@ -90,6 +90,8 @@ int tt_ctx_create(void* stream, tt_ctx** out) {
         CUDA_CHECK(cudaMalloc((void**)&c->dbarrier, 4 * sizeof(unsigned)));
         CUDA_CHECK(cudaMemset(c->dstatus, 0, sizeof(int)));
         CUDA_CHECK(cudaMemset(c->dbarrier, 0, 4 * sizeof(unsigned)));
+        CUDA_CHECK(cudaMalloc((void**)&c->dprof_flops, PROF_NSLOTS * sizeof(double)));
+        CUDA_CHECK(cudaMemset(c->dprof_flops, 0, PROF_NSLOTS * sizeof(double)));
         cudaMemPool_t pool;
         CUDA_CHECK(cudaDeviceGetDefaultMemPool(&pool, c->device));
         unsigned long long thr = ~0ULL;
@@ -113,6 +115,7 @@ int tt_ctx_destroy(tt_ctx* c) {
     cudaFreeHost(c->pinned);
     cudaFree(c->dstatus);
     cudaFree(c->dbarrier);
+    cudaFree(c->dprof_flops);
     delete c;
     return TT_OK;
 }
@@ -129,6 +132,7 @@ int tt_ctx_profile(tt_ctx* ctx, int enable) {
         ctx->pd.ms[s] = ctx->pd.flops[s] = ctx->pd.bytes[s] = 0.0;
         ctx->pd.n[s] = 0;
     }
+    CUDA_CHECK(cudaMemsetAsync(ctx->dprof_flops, 0, PROF_NSLOTS * sizeof(double), ctx->stream));
     ctx->prof = enable != 0;
     API_END
 }
@@ -137,9 +141,11 @@ int tt_ctx_prof_read(tt_ctx* ctx, int slot, long long* n, double* ms, double* fl
     API_BEGIN(ctx)
     TT_REQUIRE(ctx && slot >= 0 && slot < PROF_NSLOTS, "bad profiling slot");
     prof_resolve(ctx);
+    double dev[PROF_NSLOTS];
+    read_back(ctx, ctx->dprof_flops, dev, PROF_NSLOTS);
     if (n) *n = ctx->pd.n[slot];
     if (ms) *ms = ctx->pd.ms[slot];
-    if (flops) *flops = ctx->pd.flops[slot];
+    if (flops) *flops = ctx->pd.flops[slot] + dev[slot];
     if (bytes) *bytes = ctx->pd.bytes[slot];
     API_END
 }

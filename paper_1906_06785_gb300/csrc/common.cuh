@@ -85,6 +85,7 @@ struct tt_ctx {
     // device status word (bounded waits) + barrier counters
     int* dstatus = nullptr;
     unsigned* dbarrier = nullptr;   // [count, generation] per barrier slot
+    double* dprof_flops = nullptr;  // device-counted flops per profiling slot
 };
 
 namespace tt {

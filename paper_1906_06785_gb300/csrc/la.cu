@@ -189,6 +189,7 @@ struct QRParams {
     TC* sums;    // [L]
     unsigned* bar;
     int* status;
+    const double* fnorm;   // ||A||_F^2 (FP32 arithmetic works on A / ||A||_F), or null
 };
 
 template <typename TC>
@@ -250,9 +251,16 @@ __global__ void __launch_bounds__(256) k_qr_r(QRParams<TC> P) {
     TC* red = sm;                                   // [32]
     TC* W = P.gwork ? P.gwork + (size_t)g * P.nbp * P.c : sm + 32;   // [c][nbp]
     TC* mypart = P.part + (size_t)g * P.L;
+    // FP32 arithmetic runs on A / ||A||_F so no square overflows; R is scaled back
+    double sc = 1.0;
+    if (P.fnorm) {
+        const double f = sqrt(__ldcg(P.fnorm));   // P.fnorm holds ||A||_F^2
+        sc = (f > 0.0 && f < 1e300) ? f : 1.0;
+    }
+    const double inv = 1.0 / sc;
     for (int l = warp; l < P.c; l += nw)
         for (int i = lane; i < rows; i += 32)
-            W[(size_t)l * P.nbp + i] = TC(P.A[(long long)(row0 + i) * P.rs + (long long)l * P.cs]);
+            W[(size_t)l * P.nbp + i] = TC(P.A[(long long)(row0 + i) * P.rs + (long long)l * P.cs] * inv);
     __syncthreads();
     if (P.k > 0) qr_partials(P, W, 0, row0, rows, red, mypart);
     const int gw = g * nw + warp, TW = G * nw;
@@ -272,10 +280,13 @@ __global__ void __launch_bounds__(256) k_qr_r(QRParams<TC> P) {
         const TC ss = __ldcg(P.sums), x0 = __ldcg(P.sums + 1 + P.c + j);
         const int jloc = j - row0;
         const bool own = jloc >= 0 && jloc < rows;
-        if (ss == TC(0)) {      // zero column: R(j, :) is row j as it stands
+        // zero column (FP32: below 1e-15 of the unit-norm input, where 1 / (v^T v)
+        // would overflow): R(j, :) is row j as it stands
+        const TC zero_ss = sizeof(TC) < sizeof(double) ? TC(1e-30) : TC(0);
+        if (ss <= zero_ss) {
             if (own)
                 for (int l = tid; l < P.c; l += blockDim.x)
-                    P.R[(size_t)j * P.ldr + l] = l < j ? 0.0 : (double)W[(size_t)l * P.nbp + jloc];
+                    P.R[(size_t)j * P.ldr + l] = l < j ? 0.0 : (double)W[(size_t)l * P.nbp + jloc] * sc;
         } else {
             const TC sigma = sqrt(ss);
             const TC alpha = x0 >= TC(0) ? -sigma : sigma;
@@ -291,14 +302,35 @@ __global__ void __launch_bounds__(256) k_qr_r(QRParams<TC> P) {
                     const TC vi = (row0 + i == j) ? v0 : wj[i];
                     col[i] -= vi * wl;
                 }
-                if (own && lane == 0) P.R[(size_t)j * P.ldr + l] = (double)(el - v0 * wl);
+                if (own && lane == 0) P.R[(size_t)j * P.ldr + l] = (double)(el - v0 * wl) * sc;
             }
             if (own)
                 for (int l = tid; l <= j; l += blockDim.x)
-                    P.R[(size_t)j * P.ldr + l] = l < j ? 0.0 : (double)alpha;
+                    P.R[(size_t)j * P.ldr + l] = l < j ? 0.0 : (double)alpha * sc;
         }
         __syncthreads();
         if (j + 1 < P.k) qr_partials(P, W, j + 1, row0, rows, red, mypart);
+    }
+}
+
+// sum of squares of a strided n x cols matrix, accumulated into *out (zeroed by the caller)
+__global__ void k_frob2_strided(int n, int cols, const double* __restrict__ A, long long rs, long long cs,
+                                double* __restrict__ out) {
+    double s = 0.0;
+    const long long len = (long long)n * cols;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len; t += (long long)gridDim.x * blockDim.x) {
+        const long long i = t % n, l = t / n;
+        const double x = A[i * rs + l * cs];
+        s = fma(x, x, s);
+    }
+    __shared__ double red[32];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        s = warp_sum(s);
+        if (threadIdx.x == 0) atomicAdd(out, s);
     }
 }
 
@@ -320,6 +352,15 @@ void qr_r_launch(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr) {
     }
     const int L = 2 * cols + 1;
     DBuf<TC> scratch(c, (size_t)G * L + L);
+    DBuf<double> fn;
+    if (sizeof(TC) < sizeof(double)) {
+        fn.alloc(c, 1);
+        CUDA_CHECK(cudaMemsetAsync(fn.p, 0, sizeof(double), c->stream));
+        const long long len = (long long)n * cols;
+        const int fb = (int)std::min<long long>(2LL * c->nsm, std::max(1LL, (len + 255) / 256));
+        k_frob2_strided<<<fb, 256, 0, c->stream>>>(n, cols, A.p, A.s0, A.s1, fn.p);
+        LAUNCH_CHECK(c);
+    }
     QRParams<TC> P;
     P.n = n; P.c = cols; P.k = k; P.nb = nb; P.nbp = nbp; P.L = L;
     P.A = A.p; P.rs = A.s0; P.cs = A.s1;
@@ -329,6 +370,7 @@ void qr_r_launch(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr) {
     P.sums = scratch.p + (size_t)G * L;
     P.bar = c->dbarrier;
     P.status = c->dstatus;
+    P.fnorm = fn.p;
     CUDA_CHECK(cudaMemsetAsync(c->dbarrier, 0, 2 * sizeof(unsigned), c->stream));
     CUDA_CHECK(cudaFuncSetAttribute(k_qr_r<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     // Householder R factor: 2 n c^2 - 2 c^3 / 3 flops (n >= c); reads A once, writes R
@@ -351,8 +393,10 @@ void qr_r(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr) {
 namespace {
 __global__ void __launch_bounds__(128)
 k_jacobi(int m, int n, int npad, double* W, int ldw, int* flags, int max_sweeps, double tol,
-         unsigned* bar, int* status, int* sweeps_used, const double* frob2) {
+         unsigned* bar, int* status, int* sweeps_used, const double* frob2, double* dn,
+         double* flop_counter) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double myflops = 0.0;   // FP64 flops this warp performs (exact algorithmic count)
     const int gw = blockIdx.x * nw + warp, TW = gridDim.x * nw;
     const int P = npad / 2, NR = npad - 1;
     // columns below 1e-15 ||A||_F are numerically zero: their pair products are noise
@@ -361,6 +405,20 @@ k_jacobi(int m, int n, int npad, double* W, int ldw, int* flags, int max_sweeps,
     int sw = 0;
     for (; sw < max_sweeps; ++sw) {
         int any = 0;
+        // squared column norms, computed at the start of the sweep and refreshed by
+        // each rotation, which touches the pair anyway
+        for (int col = gw; col < n; col += TW) {
+            const double* cc = W + (size_t)col * ldw;
+            double s = 0.0;
+            for (int i = lane; i < m; i += 32) {
+                const double x = __ldcg(cc + i);
+                s = fma(x, x, s);
+            }
+            s = warp_sum(s);
+            if (lane == 0) dn[col] = s;
+            myflops += 2.0 * m;
+        }
+        grid_barrier(bar, gridDim.x, status);
         for (int r = 0; r < NR; ++r) {
             for (int p = gw; p < P; p += TW) {
                 int a, b;
@@ -368,21 +426,33 @@ k_jacobi(int m, int n, int npad, double* W, int ldw, int* flags, int max_sweeps,
                 if (a >= n || b >= n) continue;
                 double* ca = W + (size_t)a * ldw;
                 double* cb = W + (size_t)b * ldw;
-                double al = 0.0, be = 0.0, ga = 0.0;
-                for (int i = lane; i < m; i += 32) {
-                    const double x = __ldcg(ca + i), y = __ldcg(cb + i);
-                    al = fma(x, x, al); be = fma(y, y, be); ga = fma(x, y, ga);
-                }
-                al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
+                const double al = __ldcg(dn + a), be = __ldcg(dn + b);
+                double ga = 0.0;
+                for (int i = lane; i < m; i += 32) ga = fma(__ldcg(ca + i), __ldcg(cb + i), ga);
+                ga = warp_sum(ga);
+                myflops += 2.0 * m;
                 if (al > tiny && be > tiny && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
                     const double zeta = (be - al) / (2.0 * ga);
                     const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                     const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+                    double na = 0.0, nb = 0.0;
                     for (int i = lane; i < m; i += 32) {
                         const double x = __ldcg(ca + i), y = __ldcg(cb + i);
-                        ca[i] = cs * x - sn * y;
-                        cb[i] = sn * x + cs * y;
+                        const double xn = cs * x - sn * y, yn = sn * x + cs * y;
+                        ca[i] = xn;
+                        cb[i] = yn;
+                        na = fma(xn, xn, na);
+                        nb = fma(yn, yn, nb);
                     }
+                    // exact norms of the rotated pair, taken in the same pass (the closed
+                    // form |a|^2 - t a.b cancels badly for nearly dependent columns)
+                    na = warp_sum(na);
+                    nb = warp_sum(nb);
+                    if (lane == 0) {
+                        dn[a] = na;
+                        dn[b] = nb;
+                    }
+                    myflops += 10.0 * m;
                     any = 1;
                 }
             }
@@ -394,6 +464,7 @@ k_jacobi(int m, int n, int npad, double* W, int ldw, int* flags, int max_sweeps,
         if (*(volatile int*)status != DEV_OK) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_used = sw;
+    if (lane == 0 && flop_counter) atomicAdd(flop_counter, myflops);
 }
 
 __global__ void k_frob2(long long len, const double* __restrict__ W, double* __restrict__ out) {
@@ -480,10 +551,14 @@ static void jacobi_columns(tt_ctx* c, int m, int n, double* W, double* sig, doub
     int* st = c->dstatus;
     int* fl = flags.p;
     double* f2 = frob2.p;
-    void* args[] = {&mm, &nn, &np_, &W, &ld, &fl, &ms, &tol, &bar, &st, &sweeps, &f2};
+    DBuf<double> dnorm(c, n);
+    double* dnp = dnorm.p;
+    double* fc = c->prof ? c->dprof_flops + PROF_JACOBI : nullptr;
+    void* args[] = {&mm, &nn, &np_, &W, &ld, &fl, &ms, &tol, &bar, &st, &sweeps, &f2, &dnp, &fc};
     if (n > 1) {
         // one sweep: n(n-1)/2 pairs x (3 dots + 1 rotation) over m rows = 12 m flops per pair
-        ProfScope prof(c, PROF_JACOBI, 6.0 * n * (n - 1.0) * m, 16.0 * (double)m * n);
+        // flops are counted on the device (dots, rotations and norm passes performed)
+        ProfScope prof(c, PROF_JACOBI, 0.0, 16.0 * (double)m * n);
         CUDA_CHECK(cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(G), dim3(32 * wpb), args, 0, c->stream));
         count_launch(c);
         static const bool log = getenv("TT_LOG_ROUND") != nullptr;
