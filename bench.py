@@ -1,11 +1,19 @@
-"""Benchmark of the low-rank all-at-once Picard solve (plain FP64 GPU path).
+"""Benchmark of the low-rank all-at-once Picard solve (Algorithm 3.1 with the
+low-rank GMRES of Algorithm 4.2 and the mean-based LSC preconditioner).
 
-Workload: the "medium" problem -- symmetric step L=5, Q2-Q1 on element side
-1/8 (velocity spacing 1/16: n_u = 5440, n_p = 769), m = 3 KL terms, total
-degree 3 (n_xi = 20), n_t = 100, tau = 0.05, nu0 = 1/100, sigma = 0.2,
-truncation 1e-5, Table 5.2 tolerances otherwise.  One step is one complete
-Picard solve to ||r|| <= 1e-5 ||f|| (Stokes start, TT-GMRES with the mean-based
-LSC preconditioner, truncated updates), inputs resident on the GPU.
+One step is one complete Picard solve to ||r|| <= 1e-5 ||f||: Stokes start,
+TT-GMRES per Picard step with the preconditioner's inner solve, truncated
+updates and the untruncated residual, with the problem already resident on the
+GPU.  Default workload "small": symmetric step L=5, Q2-Q1 on element side 1/4
+(velocity spacing 1/8: n_u = 1312, n_p = 209), m = 2 KL terms, total degree 2
+(n_xi = 6), n_t = 20, tau = 0.1, nu0 = 1/50, sigma = 0.1, truncation 1e-6.
+`--workload medium` (n_u = 5440, n_xi = 20, n_t = 100) runs the same step on the
+larger problem; one medium solve takes tens of minutes, far beyond a short run.
+
+The timed value is the solve time on the precision chosen by --precision
+(default mixed); the other precision is timed the same way and reported beside
+it ("fp64_value" / "mixed_value"), as is the relative difference of the two
+solutions.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -30,8 +38,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "Picard-solve time to rel.res 1e-5, medium workload"
-WORKLOAD = "medium"
+METRIC = "Picard-solve time to rel.res 1e-5"
+WORKLOAD = "small"
+DESCR = {
+    "small": "small: step L=5 elem 1/4 (n_u=1312 n_p=209) m=2 d=2 n_xi=6 n_t=20 tau=0.1 nu0=1/50 sigma=0.1 eps=1e-6",
+    "medium": "medium: step L=5 elem 1/8 (n_u=5440 n_p=769) m=3 d=3 n_xi=20 n_t=100 tau=0.05 nu0=1/100 "
+              "sigma=0.2 eps=1e-5",
+}
 # ncu dram bytes (read + write) per launch of the dominant kernel class, from the
 # capture summarised in profiles/; None until measured for the current kernel.
 NCU_TRAFFIC = {}
@@ -101,31 +114,41 @@ class Clocks:
 
 # ------------------------------------------------------------------ CPU oracle sample
 def _oracle_sample_worker(workload, seconds, q):
-    """Time the oracle on a bounded sample of the workload: outer TT-GMRES
-    iterations of the Stokes solve (each: preconditioner with its inner solve,
-    matvec, truncations, Gram-Schmidt, iterate and true residual), until
+    """Time the oracle on a bounded sample of the workload: its complete Stokes
+    solve (the start of Algorithm 3.1), then outer TT-GMRES iterations of the first
+    Picard step (each: preconditioner with its inner solve, matvec with the
+    convection term, truncations, Gram-Schmidt, iterate and true residual) until
     `seconds` of CPU work have been spent."""
     for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[v] = "1"
+    import numpy as np
     import synth
     from oracle.system import Discretisation
     from oracle.solver import MeanLSC, gmres, _Pair
+    from oracle.tt import round_tt, norm
     prob = synth.preset(workload)
     d = Discretisation(prob)
     t = prob.tol
-    f = d.rhs()
-    its = 0
+    fu, fp = d.rhs()
+    fnorm = float(np.hypot(norm(fu), norm(fp)))
     t0 = time.perf_counter()
-    per = []
+    P = MeanLSC(d, None, t.eps_gmres, t.tol_inner, t.maxit_inner)
+    (u, p), st = gmres(lambda v: d.apply(None, *v), P, (fu, fp), tol=t.tol_gmres, eps=t.eps_gmres,
+                       maxit=t.maxit_gmres, space=_Pair, bnorm=fnorm)
+    r, rn = d.residual(u, p, t.eps_gmres)
+    stokes = time.perf_counter() - t0
+    wt, _ = round_tt(d.full_velocity(u), t.eps_conv)
+    per, its = [], 0
     for k in range(1, t.maxit_gmres + 1):
-        P = MeanLSC(d, None, t.eps_gmres, t.tol_inner, t.maxit_inner)
         a = time.perf_counter()
-        _, st = gmres(lambda v: d.apply(None, *v), P, f, tol=0.0, eps=t.eps_gmres, maxit=k, space=_Pair)
-        per.append((time.perf_counter() - a) / max(st["its"], 1))
-        its = st["its"]
-        if time.perf_counter() - t0 > seconds or st["its"] < k:
+        P = MeanLSC(d, wt, t.eps_gmres, t.tol_inner, t.maxit_inner)
+        _, st2 = gmres(lambda v: d.apply(wt, *v), P, r, tol=0.0, eps=t.eps_gmres, maxit=k, space=_Pair, bnorm=rn)
+        per.append((time.perf_counter() - a) / max(st2["its"], 1))
+        its = st2["its"]
+        if time.perf_counter() - t0 > seconds or st2["its"] < k:
             break
-    q.put(dict(sec_per_outer_it=per[-1], outer_its_sampled=its, wall=time.perf_counter() - t0))
+    q.put(dict(stokes_s=stokes, stokes_its=st["its"], sec_per_outer_it=per[-1], outer_its_sampled=its,
+               wall=time.perf_counter() - t0))
 
 
 def cpu_sample(workload, seconds):
@@ -161,39 +184,55 @@ def run_ours(a):
     prob = synth.preset(a.workload)
     ctx = binding.Context()
     P = ctx.problem(prob)
-    opts = binding.opts_from(prob.tol, mixed=1 if a.precision == "mixed" else 0)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     stream = torch.cuda.current_stream()
 
-    last = None
-    for _ in range(a.warmup):
-        last = P.picard(opts)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
+    def timed(mixed, profile):
+        opts = binding.opts_from(prob.tol, mixed=mixed)
+        last = None
+        for _ in range(a.warmup):
+            last = P.picard(opts)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if profile:
+            ctx.profile(True)
+        l0 = ctx.launches
+        times = []
+        for _ in range(a.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            last = P.picard(opts)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1000.0)
+        launches = (ctx.launches - l0) // max(a.steps, 1)
+        prof = None
+        if profile:
+            prof = ctx.prof_read()
+            ctx.profile(False)
+        t = sum(times) / len(times)
+        if dist:
+            tt = torch.tensor([t], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        return t, launches, prof, last, opts
+
+    main_mixed = 1 if a.precision == "mixed" else 0
+    # the other precision first, unprofiled; then the headline precision with clocks
+    t_other, _, _, last_other, _ = timed(1 - main_mixed, False)
     clocks = Clocks(local)
-    ctx.profile(True)
-    l0 = ctx.launches
-    times = []
-    for _ in range(a.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        last = P.picard(opts)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1) / 1000.0)
-    launches = (ctx.launches - l0) // max(a.steps, 1)
-    prof = ctx.prof_read()
-    ctx.profile(False)
+    t_step, launches, prof, last, opts = timed(main_mixed, True)
     clk = clocks.stop()
-    t_step = sum(times) / len(times)
-    if dist:
-        tt = torch.tensor([t_step], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
     u, p, st, code = last
+    uo, po, _, _ = last_other
+    # relative difference of the two solutions ((u, p) jointly, via TT dots)
+    dt = ctx.dot
+    du = dt(u, u) - 2 * dt(u, uo) + dt(uo, uo)
+    dp = dt(p, p) - 2 * dt(p, po) + dt(po, po)
+    rel_diff = float(np.sqrt(max(du + dp, 0.0) / (dt(uo, uo) + dt(po, po))))
 
     # end-to-end through the public API with host buffers (problem arrays in, cores out)
     e2e = []
@@ -215,7 +254,7 @@ def run_ours(a):
     dom = max(prof, key=lambda k: prof[k][1])
     n, ms, fl, by = prof[dom]
     fp64_peak = 1250.0   # GFLOP/s: nominal GB300 FP64 rate (no measured FP64 peak is available)
-    if dom == "spmm":
+    if dom in ("spmm", "band_solve"):
         achieved = by / (ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s"}
     else:
@@ -225,23 +264,26 @@ def run_ours(a):
     roof["kernel"] = dom
     roof["launches"] = n
     roof["ms_per_launch"] = ms / max(n, 1)
-    roof["traffic"] = NCU_TRAFFIC.get(dom)
-    roof["peak_source"] = ("MEASURED_PEAKS.json hbm_gbs (burst)" if roof["bound"] == "hbm"
-                           else "nominal FP64 1.25 TFLOP/s (fallback; FP64 is not in MEASURED_PEAKS.json)")
-    breakdown = {k: {"launches": v[0], "ms_per_step": v[1] / a.steps} for k, v in prof.items()}
+    roof["traffic"] = NCU_TRAFFIC.get((a.workload, dom))
+    roof["peak_source"] = ("of measured: MEASURED_PEAKS.json hbm_gbs (burst)" if roof["bound"] == "hbm"
+                           else "nominal FP64 1.25 TFLOP/s (no FP64 figure in MEASURED_PEAKS.json)")
+    breakdown = {k: {"launches": v[0], "ms_per_step": v[1] / a.steps,
+                     "gflop_per_step": v[2] / a.steps / 1e9, "gbytes_per_step": v[3] / a.steps / 1e9}
+                 for k, v in prof.items()}
 
     if rank != 0:
         return
     out = {
         "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": t_step * 1000.0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if a.precision == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": f"{a.workload}: step L=5 h=1/8 n_u={2 * prob.n_v} n_p={prob.n_p} "
-                               f"n_xi={prob.n_xi} n_t={prob.n_t}",
+        "dtype": "f32+f64" if main_mixed else "f64", "data": "synthetic",
+        "config": {"workload": DESCR.get(a.workload, a.workload),
                    "precision": "mixed (FP32 SpMM/GEMM/R factors in GMRES; FP64 SVD, dots, Hessenberg, residual)"
-                   if a.precision == "mixed" else "plain FP64",
+                   if main_mixed else "plain FP64",
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "independent replica per GPU" if world > 1 else "1 GPU"},
+        ("fp64_value" if main_mixed else "mixed_value"): t_other,
+        "rel_diff_mixed_vs_fp64": rel_diff,
         "e2e": {"value": sum(e2e) / len(e2e), "unit": "s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
@@ -253,37 +295,54 @@ def run_ours(a):
         "clocks": clk,
     }
     if cpu is not None:
-        outer = st.stokes_its + sum(st.gmres_its[1:st.picard_its + 1])
-        est = cpu["sec_per_outer_it"] * outer
+        outer = sum(st.gmres_its[1:st.picard_its + 1])
+        est = cpu["stokes_s"] + cpu["sec_per_outer_it"] * outer
         out["cpu_baseline"] = {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
-                               "sample": f"oracle Stokes-solve outer GMRES iterations on the same workload "
-                                         f"({cpu['outer_its_sampled']} its, {cpu['wall']:.1f} s), "
-                                         f"{cpu['sec_per_outer_it']:.2f} s/it x {outer} outer its of the solve"}
+                               "sample": f"oracle (1 BLAS thread) on the same workload: complete Stokes solve "
+                                         f"({cpu['stokes_s']:.1f} s) + first Picard step outer GMRES iteration(s) "
+                                         f"({cpu['outer_its_sampled']}, {cpu['sec_per_outer_it']:.1f} s each) "
+                                         f"scaled to the {outer} Picard-step outer iterations of the solve"}
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
 # ------------------------------------------------------------------ reference arm
+def _oracle_outer_its(workload):
+    """Outer GMRES iterations (Stokes + every Picard step) of the oracle's complete
+    solve of this workload, from the oracle-written golden record when there is one."""
+    path = os.path.join(ROOT, "tests", "golden", f"picard_{workload}.txt")
+    if os.path.exists(path):
+        rec = {}
+        for line in open(path):
+            if line.startswith("#") or not line.strip():
+                continue
+            k, *v = line.split()
+            rec[k] = v
+        return int(rec["stokes_its"][0]) + sum(int(x) for x in rec["gmres_its"])
+    raise SystemExit(f"no oracle solve record for workload {workload!r}")
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    per = max(5.0, 150.0 / max(a.steps + a.warmup, 1))
+    per = max(10.0, 150.0 / max(a.steps + a.warmup, 1))
     for _ in range(a.warmup):
         cpu_sample(a.workload, per)
     samples = [cpu_sample(a.workload, per) for _ in range(a.steps)]
+    outer = _oracle_outer_its(a.workload) - int(samples[0]["stokes_its"])
+    vals = [x["stokes_s"] + x["sec_per_outer_it"] * outer for x in samples]
+    v = sum(vals) / len(vals)
     s = sum(x["sec_per_outer_it"] for x in samples) / len(samples)
-    # outer iteration count of a complete solve of this workload (GPU run statistics)
-    outer = 14
-    v = s * outer
     out = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
            "ms_per_step": v * 1000.0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": a.workload, "precision": "plain FP64 (CPU oracle)"},
+           "config": {"workload": DESCR.get(a.workload, a.workload), "precision": "plain FP64 (CPU oracle)"},
            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
-                            "sample": f"{s:.2f} s per outer GMRES iteration of the Stokes solve x {outer} outer "
-                                      f"iterations per solve"},
+                            "sample": f"per step: complete oracle Stokes solve + first Picard step outer GMRES "
+                                      f"iteration(s) at {s:.1f} s each, scaled to the {outer} Picard-step outer "
+                                      f"iterations of the oracle's complete solve (1 BLAS thread)"},
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

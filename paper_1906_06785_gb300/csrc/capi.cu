@@ -1,6 +1,9 @@
 // extern "C" entry points declared in include/tt_stochns.h.  Every entry point
 // catches the library's exceptions and turns them into status codes.
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "solver.cuh"
 
@@ -16,6 +19,41 @@ void check_status(tt_ctx* c) {
         TT_THROW(TT_ENAN, "zero or non-finite pivot / value met on the device");
     }
 }
+int max_cluster_ctas(tt_ctx* c, const void* kernel, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void*, int, size_t>, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_tuple(c->device, kernel, threads, smem);
+    const auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int best = 0;
+    for (int size : {16, 8}) {
+        if (size > 8 && cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(size);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = size;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) == cudaSuccess && n > 0) {
+            best = size;
+            break;
+        }
+        (void)cudaGetLastError();
+    }
+    cache[key] = best;
+    return best;
+}
+
 static cudaEvent_t ev_get(tt_ctx* c) {
     if (!c->pd.pool.empty()) {
         cudaEvent_t e = c->pd.pool.back();

@@ -69,8 +69,9 @@ struct tt_ctx {
     bool prof = false;
     ProfData pd;
     // Compute precision of the SpMM, GEMM, Householder R factor and banded solves:
-    // 0 = FP64, 1 = FP32 arithmetic on FP64-stored data (the mixed path).  Jacobi
-    // SVDs, inner products, Hessenberg solves and band factorisations are FP64 always.
+    // 0 = FP64, 1 = FP32 arithmetic on FP64-stored data (the mixed path).  SVDs
+    // (with their R factors), inner products, Hessenberg solves and band
+    // factorisations are FP64 always.
     int fast = 0;
     // Truncations with eps >= 5e-6 may take the Gram route (FP64 GEMMs and
     // eigenpairs of small Gram matrices instead of Householder R factors).
@@ -207,6 +208,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 // return at once, so a kernel that lost a block still terminates.
 __device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
     __syncthreads();
+    if (nblocks == 1) return;   // a one-block launch needs only the block barrier
     if (threadIdx.x == 0) {
         volatile unsigned* vgen = bar + 1;
         unsigned gen = *vgen;
@@ -232,6 +234,26 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, in
     }
     __syncthreads();
 }
+
+// Barrier across all CTAs of a launch.  kCluster: the launch is one thread-block
+// cluster and the hardware cluster barrier (release/acquire at cluster scope, which
+// orders the CTAs' global and shared memory accesses) replaces the software grid
+// barrier; every CTA of a cluster is resident by construction, so it cannot wait
+// on an absent CTA.
+template <bool kCluster>
+__device__ __forceinline__ void group_barrier(unsigned* bar, unsigned nblocks, int* status) {
+    if constexpr (kCluster) {
+        __syncthreads();
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    } else {
+        grid_barrier(bar, nblocks, status);
+    }
+}
 #endif
+
+// Largest single-cluster grid (CTAs) that can run `kernel` with `threads` threads and
+// `smem` bytes of dynamic shared memory per CTA on this device: 16 when the
+// non-portable size is schedulable, else 8, else 0 (no cluster launch).
+int max_cluster_ctas(tt_ctx* c, const void* kernel, int threads, size_t smem);
 
 }  // namespace tt

@@ -8,8 +8,9 @@
 //    memory when it fits) and, per column, the CTAs exchange partial norms and
 //    partial reflector dots through global memory across bounded grid
 //    barriers (a flat-tree TSQR in which the tree is one reduction level).
-//  * left_svd: one-sided (Hestenes) Jacobi, columns rotated pairwise in
-//    round-robin order, one warp per pair, one grid barrier per round.
+//  * left_svd: R factor of A^T, then one-sided (Hestenes) Jacobi on R^T,
+//    columns rotated pairwise in round-robin order, one warp per pair, one grid
+//    barrier per round.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -240,7 +241,7 @@ __device__ void qr_partials(const QRParams<TC>& P, const TC* W, int j, int row0,
 // Householder with one combined reduction per column: v^T a_l = a_j^T a_l - alpha a_jl
 // lets the norm of column j, its products with the trailing columns and row j travel
 // together, so each column costs two grid barriers (partials ready, sums ready).
-template <typename TC>
+template <typename TC, bool kCluster>
 __global__ void __launch_bounds__(256) k_qr_r(QRParams<TC> P) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     TC* sm = reinterpret_cast<TC*>(sm_raw);
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(256) k_qr_r(QRParams<TC> P) {
     const int gw = g * nw + warp, TW = G * nw;
     for (int j = 0; j < P.k; ++j) {
         if (*(volatile int*)P.status != DEV_OK) return;
-        grid_barrier(P.bar, G, P.status);
+        group_barrier<kCluster>(P.bar, G, P.status);
         // reduce-scatter of the live entries: 0, 1 + (j, c), 1 + c + [j, c)
         const int nd = P.c - j - 1, ne = P.c - j;
         for (int t = gw; t < 1 + nd + ne; t += TW) {
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(256) k_qr_r(QRParams<TC> P) {
             s = warp_sum(s);
             if (lane == 0) P.sums[idx] = s;
         }
-        grid_barrier(P.bar, G, P.status);
+        group_barrier<kCluster>(P.bar, G, P.status);
         const TC ss = __ldcg(P.sums), x0 = __ldcg(P.sums + 1 + P.c + j);
         const int jloc = j - row0;
         const bool own = jloc >= 0 && jloc < rows;
@@ -338,6 +339,11 @@ template <typename TC>
 void qr_r_launch(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr) {
     const int k = std::min(n, cols);
     int G = std::min(c->nsm, std::max(1, ceil_div(n, 16)));
+    // Small panels run in one CTA: its columns then cost two block barriers instead
+    // of two grid barriers (~2 us each), which dominate below ~4k (FP64: one SM's
+    // FP64 rate is low) or ~48k (FP32) entries.
+    const long long small_entries = sizeof(TC) < sizeof(double) ? 48 * 1024 : 4 * 1024;
+    if ((long long)n * cols <= small_entries) G = 1;
     const int nb = ceil_div(n, G);
     G = ceil_div(n, nb);
     const int nbp = nb | 1;
@@ -372,13 +378,32 @@ void qr_r_launch(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr) {
     P.status = c->dstatus;
     P.fnorm = fn.p;
     CUDA_CHECK(cudaMemsetAsync(c->dbarrier, 0, 2 * sizeof(unsigned), c->stream));
-    CUDA_CHECK(cudaFuncSetAttribute(k_qr_r<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    CUDA_CHECK(cudaFuncSetAttribute(k_qr_r<TC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    CUDA_CHECK(cudaFuncSetAttribute(k_qr_r<TC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     // Householder R factor: 2 n c^2 - 2 c^3 / 3 flops (n >= c); reads A once, writes R
     const double kk = k;
     ProfScope prof(c, PROF_QR, 2.0 * kk * kk * ((double)n + cols - kk) - 2.0 * kk * kk * kk / 3.0,
                    8.0 * ((double)n * cols + kk * cols));
-    void* args[] = {&P};
-    CUDA_CHECK(cudaLaunchCooperativeKernel((void*)k_qr_r<TC>, dim3(G), dim3(256), args, smem, c->stream));
+    // a grid that fits in one thread-block cluster synchronises with the hardware
+    // cluster barrier (~10x cheaper than the grid barrier); larger grids are cooperative
+    if (G > 1 && G <= max_cluster_ctas(c, (const void*)k_qr_r<TC, true>, 256, smem)) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(G);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = c->stream;
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = G;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        CUDA_CHECK(cudaLaunchKernelEx(&cfg, k_qr_r<TC, true>, P));
+    } else {
+        void* args[] = {&P};
+        CUDA_CHECK(cudaLaunchCooperativeKernel((void*)k_qr_r<TC, false>, dim3(G), dim3(256), args, smem, c->stream));
+    }
     count_launch(c);
 }
 }  // namespace
@@ -391,75 +416,97 @@ void qr_r(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr) {
 
 // ============================================================== Jacobi SVD
 namespace {
+// Rotation of the column pair (a, b) of a one-sided Jacobi sweep, by one warp.
+// Dot products and norms run over rows [0, m); the rotation is applied to rows
+// [0, mr), mr >= m (rows m..mr-1 accumulate V when the caller needs it).  The
+// squared norms in dn are refreshed from the rotated columns in the same pass.
+// Returns whether the pair was rotated.  kGlobal: W and dn live in global memory
+// shared by several CTAs (reads bypass L1).
+template <typename T, bool kGlobal>
+__device__ __forceinline__ T jld(const T* p) {
+    if constexpr (kGlobal) return __ldcg(p);
+    else return *p;
+}
+template <typename T, bool kGlobal>
+__device__ __forceinline__ bool jacobi_pair(T* ca, T* cb, int a, int b, int m, int mr, T* dn, T tol, T tiny,
+                                            double& flops) {
+    const int lane = threadIdx.x & 31;
+    const T al = jld<T, kGlobal>(dn + a), be = jld<T, kGlobal>(dn + b);
+    T ga = T(0);
+    for (int i = lane; i < m; i += 32) ga = fma(jld<T, kGlobal>(ca + i), jld<T, kGlobal>(cb + i), ga);
+    ga = warp_sum(ga);
+    flops += 2.0 * m;
+    if (!(al > tiny && be > tiny && fabs(ga) > tol * sqrt(al) * sqrt(be))) return false;
+    const T zeta = (be - al) / (T(2) * ga);
+    const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+    const T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
+    T na = T(0), nb = T(0);
+    for (int i = lane; i < mr; i += 32) {
+        const T x = jld<T, kGlobal>(ca + i), y = jld<T, kGlobal>(cb + i);
+        const T xn = cs * x - sn * y, yn = sn * x + cs * y;
+        ca[i] = xn;
+        cb[i] = yn;
+        if (i < m) {
+            na = fma(xn, xn, na);
+            nb = fma(yn, yn, nb);
+        }
+    }
+    na = warp_sum(na);
+    nb = warp_sum(nb);
+    if (lane == 0) {
+        dn[a] = na;
+        dn[b] = nb;
+    }
+    flops += 6.0 * mr + 4.0 * m;
+    return true;
+}
+
+// Round-robin (circle) pairing: round r pairs (r, npad-1) and ((r+p) mod (npad-1),
+// (r-p) mod (npad-1)) for p = 1 .. npad/2-1; a column index >= n is a dummy.
+__device__ __forceinline__ void circle_pair(int r, int p, int NR, int& a, int& b) {
+    if (p == 0) { a = r; b = NR; } else { a = (r + p) % NR; b = (r - p + NR) % NR; }
+}
+
+// Sweeps over the whole grid: one warp per pair, a grid-wide barrier per round (the
+// cluster barrier when the grid is one cluster, else the cooperative grid barrier).
+// Columns with squared norm <= tiny_rel * frob2 are numerically zero and not rotated.
+template <typename T, bool kCluster>
 __global__ void __launch_bounds__(128)
-k_jacobi(int m, int n, int npad, double* W, int ldw, int* flags, int max_sweeps, double tol,
-         unsigned* bar, int* status, int* sweeps_used, const double* frob2, double* dn,
-         double* flop_counter) {
+k_jacobi(int m, int mr, int n, int npad, T* W, int ldw, int* flags, int max_sweeps, T tol, double tiny_rel,
+         unsigned* bar, int* status, int* sweeps_used, const double* frob2, T* dn, double* flop_counter) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    double myflops = 0.0;   // FP64 flops this warp performs (exact algorithmic count)
+    double myflops = 0.0;   // flops this warp performs (exact algorithmic count)
     const int gw = blockIdx.x * nw + warp, TW = gridDim.x * nw;
     const int P = npad / 2, NR = npad - 1;
-    // columns below 1e-15 ||A||_F are numerically zero: their pair products are noise
-    // and are not rotated (otherwise the sweep never meets the threshold)
-    const double tiny = 1e-30 * __ldcg(frob2);
+    const T tiny = T(tiny_rel * __ldcg(frob2));
     int sw = 0;
     for (; sw < max_sweeps; ++sw) {
         int any = 0;
-        // squared column norms, computed at the start of the sweep and refreshed by
-        // each rotation, which touches the pair anyway
         for (int col = gw; col < n; col += TW) {
-            const double* cc = W + (size_t)col * ldw;
-            double s = 0.0;
+            const T* cc = W + (size_t)col * ldw;
+            T s = T(0);
             for (int i = lane; i < m; i += 32) {
-                const double x = __ldcg(cc + i);
+                const T x = __ldcg(cc + i);
                 s = fma(x, x, s);
             }
             s = warp_sum(s);
             if (lane == 0) dn[col] = s;
             myflops += 2.0 * m;
         }
-        grid_barrier(bar, gridDim.x, status);
+        group_barrier<kCluster>(bar, gridDim.x, status);
         for (int r = 0; r < NR; ++r) {
             for (int p = gw; p < P; p += TW) {
                 int a, b;
-                if (p == 0) { a = r; b = NR; } else { a = (r + p) % NR; b = (r - p + NR) % NR; }
+                circle_pair(r, p, NR, a, b);
                 if (a >= n || b >= n) continue;
-                double* ca = W + (size_t)a * ldw;
-                double* cb = W + (size_t)b * ldw;
-                const double al = __ldcg(dn + a), be = __ldcg(dn + b);
-                double ga = 0.0;
-                for (int i = lane; i < m; i += 32) ga = fma(__ldcg(ca + i), __ldcg(cb + i), ga);
-                ga = warp_sum(ga);
-                myflops += 2.0 * m;
-                if (al > tiny && be > tiny && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-                    const double zeta = (be - al) / (2.0 * ga);
-                    const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                    const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-                    double na = 0.0, nb = 0.0;
-                    for (int i = lane; i < m; i += 32) {
-                        const double x = __ldcg(ca + i), y = __ldcg(cb + i);
-                        const double xn = cs * x - sn * y, yn = sn * x + cs * y;
-                        ca[i] = xn;
-                        cb[i] = yn;
-                        na = fma(xn, xn, na);
-                        nb = fma(yn, yn, nb);
-                    }
-                    // exact norms of the rotated pair, taken in the same pass (the closed
-                    // form |a|^2 - t a.b cancels badly for nearly dependent columns)
-                    na = warp_sum(na);
-                    nb = warp_sum(nb);
-                    if (lane == 0) {
-                        dn[a] = na;
-                        dn[b] = nb;
-                    }
-                    myflops += 10.0 * m;
+                if (jacobi_pair<T, true>(W + (size_t)a * ldw, W + (size_t)b * ldw, a, b, m, mr, dn, tol, tiny,
+                                         myflops))
                     any = 1;
-                }
             }
-            grid_barrier(bar, gridDim.x, status);
+            group_barrier<kCluster>(bar, gridDim.x, status);
         }
         if (any && lane == 0) flags[sw] = 1;
-        grid_barrier(bar, gridDim.x, status);
+        group_barrier<kCluster>(bar, gridDim.x, status);
         if (__ldcg(flags + sw) == 0) break;
         if (*(volatile int*)status != DEV_OK) break;
     }
@@ -528,45 +575,68 @@ __global__ void k_permute_normalise(int m, int n, const double* __restrict__ W, 
 }
 }  // namespace
 
-static void jacobi_columns(tt_ctx* c, int m, int n, double* W, double* sig, double* U, double ortho_tol) {
-    // W: m x n column-major (ld m), overwritten by W V (orthogonal columns)
+template <typename T>
+static void jacobi_grid(tt_ctx* c, int m, int mr, int n, T* W, int ldw, T tol, double tiny_rel,
+                        const double* frob2, int max_sweeps, double* fc, const char* tag) {
     const int npad = n + (n & 1);
-    const int P = npad / 2;
     const int wpb = 4;
-    const int G = std::max(1, std::min(c->nsm, ceil_div(P, wpb)));
-    const int max_sweeps = 60;
+    const int G = std::max(1, std::min(c->nsm, ceil_div(npad / 2, wpb)));
     DBuf<int> flags(c, max_sweeps + 1);
     CUDA_CHECK(cudaMemsetAsync(flags.p, 0, (max_sweeps + 1) * sizeof(int), c->stream));
     CUDA_CHECK(cudaMemsetAsync(c->dbarrier, 0, 2 * sizeof(unsigned), c->stream));
-    // Orthogonality target: FP64 dot products of nearly orthogonal columns carry
-    // rounding noise of order m eps_mach, so a tighter target only re-rotates noise;
-    // 1e-13 relative is far below any truncation tolerance used here.
-    double tol = std::max(ortho_tol, 4.0 * m * 2.220446049250313e-16);
+    DBuf<T> dn(c, n);
     int* sweeps = flags.p + max_sweeps;
-    DBuf<double> frob2(c, 1);
-    k_frob2<<<1, 256, 0, c->stream>>>((long long)m * n, W, frob2.p);
-    LAUNCH_CHECK(c);
-    int mm = m, nn = n, np_ = npad, ld = m, ms = max_sweeps;
+    int mm = m, mmr = mr, nn = n, np_ = npad, ld = ldw, ms = max_sweeps;
+    T tl = tol;
+    double tr = tiny_rel;
     unsigned* bar = c->dbarrier;
     int* st = c->dstatus;
     int* fl = flags.p;
-    double* f2 = frob2.p;
-    DBuf<double> dnorm(c, n);
-    double* dnp = dnorm.p;
-    double* fc = c->prof ? c->dprof_flops + PROF_JACOBI : nullptr;
-    void* args[] = {&mm, &nn, &np_, &W, &ld, &fl, &ms, &tol, &bar, &st, &sweeps, &f2, &dnp, &fc};
+    const double* f2 = frob2;
+    T* dnp = dn.p;
+    if (G > 1 && G <= max_cluster_ctas(c, (const void*)k_jacobi<T, true>, 32 * wpb, 0)) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(G);
+        cfg.blockDim = dim3(32 * wpb);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = c->stream;
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = G;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        CUDA_CHECK(cudaLaunchKernelEx(&cfg, k_jacobi<T, true>, mm, mmr, nn, np_, W, ld, fl, ms, tl, tr, bar, st,
+                                      sweeps, f2, dnp, fc));
+    } else {
+        void* args[] = {&mm, &mmr, &nn, &np_, &W, &ld, &fl, &ms, &tl, &tr, &bar, &st, &sweeps, &f2, &dnp, &fc};
+        CUDA_CHECK(cudaLaunchCooperativeKernel((void*)k_jacobi<T, false>, dim3(G), dim3(32 * wpb), args, 0,
+                                               c->stream));
+    }
+    count_launch(c);
+    static const bool log = getenv("TT_LOG_ROUND") != nullptr;
+    if (log) {
+        int sw = 0;
+        read_back(c, (const int*)sweeps, &sw, 1);
+        fprintf(stderr, "jacobi%s m=%d n=%d sweeps=%d\n", tag, m, n, sw);
+    }
+}
+
+static void jacobi_columns(tt_ctx* c, int m, int n, double* W, double* sig, double* U, double ortho_tol) {
+    // W: m x n column-major (ld m), overwritten by W V (orthogonal columns)
+    const int max_sweeps = 60;
+    // Orthogonality target: FP64 dot products of nearly orthogonal columns carry
+    // rounding noise of order m eps_mach, so a tighter target only re-rotates noise.
+    const double tol = std::max(ortho_tol, 4.0 * m * 2.220446049250313e-16);
+    DBuf<double> frob2(c, 1);
+    k_frob2<<<1, 256, 0, c->stream>>>((long long)m * n, W, frob2.p);
+    LAUNCH_CHECK(c);
     if (n > 1) {
-        // one sweep: n(n-1)/2 pairs x (3 dots + 1 rotation) over m rows = 12 m flops per pair
         // flops are counted on the device (dots, rotations and norm passes performed)
         ProfScope prof(c, PROF_JACOBI, 0.0, 16.0 * (double)m * n);
-        CUDA_CHECK(cudaLaunchCooperativeKernel((void*)k_jacobi, dim3(G), dim3(32 * wpb), args, 0, c->stream));
-        count_launch(c);
-        static const bool log = getenv("TT_LOG_ROUND") != nullptr;
-        if (log) {
-            int sw = 0;
-            read_back(c, (const int*)sweeps, &sw, 1);
-            fprintf(stderr, "jacobi m=%d n=%d sweeps=%d\n", m, n, sw);
-        }
+        jacobi_grid<double>(c, m, m, n, W, m, tol, 1e-30, frob2.p, max_sweeps,
+                            c->prof ? c->dprof_flops + PROF_JACOBI : nullptr, "");
     }
     DBuf<double> nrm(c, n);
     DBuf<int> rank(c, n);
@@ -580,23 +650,19 @@ static void jacobi_columns(tt_ctx* c, int m, int n, double* W, double* sig, doub
 
 void left_svd(tt_ctx* c, int m, int n, MatView A, double* sig, double* U, double ortho_tol) {
     TT_REQUIRE(m > 0 && n > 0, "left_svd: empty matrix");
-    // The SVD proper (Jacobi) is FP64 always.  When n > m the m x n matrix is first
-    // reduced to an m x m triangle by an R factor, which follows the context's
-    // precision (FP32 on the mixed path).
-    if (n <= m) {
-        DBuf<double> W(c, (size_t)m * n);
-        copy_mat(c, m, n, A, colmaj(W.p, m));
-        jacobi_columns(c, m, n, W.p, sig, U, ortho_tol);
-    } else {
-        // A = R^T Q^T with A^T = Q R: left singular vectors of A are those of R^T (m x m)
-        DBuf<double> R(c, (size_t)m * m);
-        qr_r(c, n, m, trans(A), R.p, m);        // R: m x m row-major
-        DBuf<double> W(c, (size_t)m * m);
-        // W = R^T column-major: W(i, j) = R(j, i) -> element (i,j) at j*m + i = R[j*m + i]
-        CUDA_CHECK(cudaMemcpyAsync(W.p, R.p, (size_t)m * m * sizeof(double), cudaMemcpyDeviceToDevice,
-                                   c->stream));
-        jacobi_columns(c, m, m, W.p, sig, U, ortho_tol);
-    }
+    // The SVD is FP64 on both precision paths.  A^T = Q R (Householder, R is k x m
+    // with k = min(m, n)) gives A = R^T Q^T: the left singular vectors of A are those
+    // of the m x k matrix R^T, and one-sided Jacobi on R^T converges in far fewer
+    // sweeps than on A itself (the triangular factor is already close to orthogonal
+    // columns; cf. QR-preconditioned Jacobi, Drmac and Veselic 2008).
+    PrecScope fp64(c, 0);
+    const int k = std::min(m, n);
+    DBuf<double> R(c, (size_t)k * m);
+    qr_r(c, n, m, trans(A), R.p, m);        // R: k x m row-major
+    // W = R^T column-major (m x k): W(i, j) = R(j, i) at j*m + i = R[j*m + i]
+    DBuf<double> W(c, (size_t)m * k);
+    CUDA_CHECK(cudaMemcpyAsync(W.p, R.p, (size_t)m * k * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    jacobi_columns(c, m, k, W.p, sig, U, ortho_tol);
 }
 
 // ============================================================== truncation
