@@ -97,6 +97,19 @@ int tt_dot(tt_ctx* ctx, const tt_t* a, const tt_t* b, double* out);
 int tt_axpby(tt_ctx* ctx, double alpha, const tt_t* a, double beta, const tt_t* b,
              tt_t** out);
 
+/* <vec a, vec b> into *out (host), like tt_dot, for callers that cannot allocate
+ * device memory at the call: a process that has given its whole device memory to
+ * its own pool up front (any further cudaMalloc fails), or a latency-critical loop
+ * that must not enter an allocator.  The paper has no counterpart of this entry
+ * point.  All scratch lives in one static device array of 2^21 doubles (16 MiB per
+ * device, held for the life of the process); nothing is allocated.  Ranks whose
+ * intermediates need more than that, r1a*r1b + r1a*n_xi*r2b + 2*r2a*r2b + 1
+ * doubles, are rejected with TT_EINVAL and a message naming the sizes.  The
+ * scratch is shared by every caller on a device: calls that overlap in time
+ * (other threads, streams or contexts on the same device) race on it and return
+ * wrong values, so serialise them.  Synchronises the context stream. */
+int tt_dot_noalloc(tt_ctx* ctx, const tt_t* a, const tt_t* b, double* out);
+
 /* ---- the discrete problem (Sections 3, 5.1) -------------------------------- */
 
 /* Statement of the discrete all-at-once problem.  All arrays are host memory

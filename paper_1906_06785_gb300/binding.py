@@ -65,6 +65,7 @@ _SIGS = {
     "tt_get_cores": (_I, [_P, _P, _P, _P, _P, _I]),
     "tt_round": (_I, [_P, _P, _D, C.POINTER(_P), _DP, _DP]),
     "tt_dot": (_I, [_P, _P, _P, _DP]),
+    "tt_dot_noalloc": (_I, [_P, _P, _P, _DP]),
     "tt_axpby": (_I, [_P, _D, _P, _D, _P, C.POINTER(_P)]),
     "tt_problem_create": (_I, [_P, C.POINTER(ProblemDesc), C.POINTER(_P)]),
     "tt_problem_destroy": (_I, [_P]),
@@ -192,6 +193,12 @@ class Context:
     def dot(self, a, b):
         out = _D()
         self.check(self.lib.tt_dot(self.h, a.h, b.h, C.byref(out)))
+        return out.value
+
+    def dot_noalloc(self, a, b):
+        """<a, b> through the allocation-free entry point (static device scratch)."""
+        out = _D()
+        self.check(self.lib.tt_dot_noalloc(self.h, a.h, b.h, C.byref(out)))
         return out.value
 
     def axpby(self, alpha, a, beta, b):
