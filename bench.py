@@ -160,6 +160,18 @@ def cpu_sample(workload, seconds):
     return q.get()
 
 
+def max_over_ranks(value, dist=None, device="cuda"):
+    """The largest value over all ranks (the slowest rank's time); the value itself
+    with one rank.  `device` is where the collective's tensor lives ("cuda" for
+    NCCL, "cpu" for gloo)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(a):
     import numpy as np
@@ -213,11 +225,7 @@ def run_ours(a):
         if profile:
             prof = ctx.prof_read()
             ctx.profile(False)
-        t = sum(times) / len(times)
-        if dist:
-            tt = torch.tensor([t], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
+        t = max_over_ranks(sum(times) / len(times), dist, "cuda")
         return t, launches, prof, last, opts
 
     main_mixed = 1 if a.precision == "mixed" else 0
