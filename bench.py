@@ -59,6 +59,9 @@ def _args():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--batch", type=int, default=0,
+                    help="> 0: time batches of this many independent problems of the workload (seeded "
+                         "nu0 in [1/100, 1/50], sigma in [0.05, 0.3]) solved concurrently, one stream each")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="mixed: FP32 SpMM/GEMM/R factors inside GMRES, FP64 SVDs, dots, residual; "
                          "fp64: plain FP64 throughout")
@@ -315,6 +318,58 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ batched form
+def run_batch(a):
+    """Aggregate throughput of concurrent independent solves (picard_solve_batched):
+    one context and stream per problem.  The batch spans several streams, so the
+    step time is host wall-clock between two device synchronisations."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1906_06785_gb300 import binding
+
+    probs = synth.batch(a.workload, a.batch, seed=5, nu0_range=(1 / 100, 1 / 50))
+    streams = [torch.cuda.Stream() for _ in probs]
+    ctxs = [binding.Context(stream=s.cuda_stream) for s in streams]
+    handles = [c.problem(pr) for c, pr in zip(ctxs, probs)]
+    mixed = 1 if a.precision == "mixed" else 0
+    opts = [binding.opts_from(pr.tol, mixed=mixed) for pr in probs]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(a.warmup):
+        binding.picard_batched(handles, opts)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    walls, lat, codes, its = [], [], [], []
+    launches0 = sum(c.launches for c in ctxs)
+    for _ in range(a.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = binding.picard_batched(handles, opts)
+        torch.cuda.synchronize()
+        walls.append(time.perf_counter() - t0)
+        lat += [o[4] for o in out]
+        codes += [o[3] for o in out]
+        its += [o[2].picard_its for o in out]
+    clk = clocks.stop()
+    t = sum(walls) / len(walls)
+    out = {
+        "metric": f"Picard-solve throughput, {a.batch} independent problems solved concurrently",
+        "value": a.batch / t, "unit": "problems/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": t * 1000.0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": f"batch of {a.batch} x " + DESCR.get(a.workload, a.workload).split(":")[0]
+                               + " problems, nu0 log-uniform in [1/100, 1/50], sigma in [0.05, 0.3], seed 5",
+                   "l2": "flushed (256 MB write) before every timed batch", "parallelism": "1 GPU, 1 stream per problem"},
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "max": float(max(lat))},
+        "statuses": sorted(set(int(c) for c in codes)), "picard_its": its[:a.batch],
+        "gpu_launches": int((sum(c.launches for c in ctxs) - launches0) // max(a.steps, 1)),
+        "clocks": clk,
+    }
+    print(json.dumps(out), flush=True)
+
+
 # ------------------------------------------------------------------ reference arm
 def _oracle_outer_its(workload):
     """Outer GMRES iterations (Stokes + every Picard step) of the oracle's complete
@@ -359,5 +414,7 @@ if __name__ == "__main__":
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.batch > 0:
+        run_batch(args)
     else:
         run_ours(args)

@@ -238,6 +238,20 @@ int tt_gmres(tt_ctx* ctx, tt_op* op, const tt_solver_opts* opts, const tt_t* bu,
 int picard_solve(tt_ctx* ctx, tt_problem* prob, const tt_solver_opts* opts, tt_t** u,
                  tt_t** p, tt_picard_stats* stats);
 
+/* Batched form: nprob independent problems solved concurrently, each exactly as
+ * picard_solve (Algorithm 3.1) with its own options opts[i].  The paper has no
+ * batched form.  Every problem must belong to a different context (its own
+ * stream); each solve runs on its own host thread, so the latency-bound launches
+ * of one solve overlap those of the others on the GPU.  Outputs per problem:
+ * u[i], p[i] (NULL when status[i] is an error other than TT_ENOCONV), stats[i],
+ * status[i] (as picard_solve returns it) and, if seconds is not NULL,
+ * seconds[i] = wall time of that solve.  Returns TT_OK when every status is
+ * TT_OK, TT_EINVAL for bad arguments (shared contexts included, nothing run),
+ * else the first failing status. */
+int picard_solve_batched(int nprob, tt_problem* const* probs, const tt_solver_opts* opts,
+                         tt_t** u, tt_t** p, tt_picard_stats* stats, int* status,
+                         double* seconds);
+
 #ifdef __cplusplus
 }
 #endif

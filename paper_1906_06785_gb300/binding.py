@@ -82,6 +82,8 @@ _SIGS = {
                       C.POINTER(GmresStats)]),
     "picard_solve": (_I, [_P, _P, C.POINTER(SolverOpts), C.POINTER(_P), C.POINTER(_P),
                           C.POINTER(PicardStats)]),
+    "picard_solve_batched": (_I, [_I, C.POINTER(_P), C.POINTER(SolverOpts), C.POINTER(_P), C.POINTER(_P),
+                                  C.POINTER(PicardStats), _IP, _DP]),
 }
 
 
@@ -381,3 +383,29 @@ class OpHandle:
             self.close()
         except Exception:
             pass
+
+
+def picard_batched(problems, opts):
+    """Solve independent problems concurrently (picard_solve_batched).  `problems`:
+    ProblemHandles on pairwise different contexts; `opts`: one SolverOpts per problem
+    (or one for all).  Returns [(u, p, stats, status, seconds)] in input order."""
+    n = len(problems)
+    if n == 0:
+        return []
+    if isinstance(opts, SolverOpts):
+        opts = [opts] * n
+    lib = problems[0].ctx.lib
+    probs = (_P * n)(*[pr.h for pr in problems])
+    oarr = (SolverOpts * n)(*opts)
+    U, Pp = (_P * n)(), (_P * n)()
+    st = (PicardStats * n)()
+    codes, secs = (_I * n)(), (_D * n)()
+    code = lib.picard_solve_batched(n, probs, oarr, U, Pp, st, codes, secs)
+    if code == TT_EINVAL and all(c == TT_OK for c in codes):
+        problems[0].ctx._check(code)
+    out = []
+    for i, pr in enumerate(problems):
+        u = TTHandle(pr.ctx, _P(U[i])) if U[i] else None
+        p = TTHandle(pr.ctx, _P(Pp[i])) if Pp[i] else None
+        out.append((u, p, st[i], codes[i], secs[i]))
+    return out

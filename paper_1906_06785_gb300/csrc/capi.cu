@@ -1,9 +1,12 @@
 // extern "C" entry points declared in include/tt_stochns.h.  Every entry point
 // catches the library's exceptions and turns them into status codes.
+#include <chrono>
 #include <cmath>
 #include <map>
 #include <mutex>
+#include <thread>
 #include <tuple>
+#include <vector>
 
 #include "solver.cuh"
 
@@ -434,6 +437,44 @@ int picard_solve(tt_ctx* ctx, tt_problem* P, const tt_solver_opts* o, tt_t** u, 
         return TT_ENOCONV;
     }
     API_END
+}
+
+int picard_solve_batched(int nprob, tt_problem* const* probs, const tt_solver_opts* opts, tt_t** u, tt_t** p,
+                         tt_picard_stats* stats, int* status, double* seconds) {
+    if (nprob <= 0 || !probs || !opts || !u || !p || !stats || !status) return TT_EINVAL;
+    for (int i = 0; i < nprob; ++i) {
+        if (!probs[i] || !probs[i]->ctx) return TT_EINVAL;
+        u[i] = nullptr;
+        p[i] = nullptr;
+        status[i] = TT_OK;
+        if (seconds) seconds[i] = 0.0;
+    }
+    for (int i = 0; i < nprob; ++i)
+        for (int j = i + 1; j < nprob; ++j)
+            if (probs[i]->ctx == probs[j]->ctx) {
+                probs[i]->ctx->err = "picard_solve_batched: two problems share a context (stream)";
+                return TT_EINVAL;
+            }
+    std::vector<std::thread> workers;
+    workers.reserve(nprob);
+    for (int i = 0; i < nprob; ++i) {
+        workers.emplace_back([=]() {
+            tt_ctx* c = probs[i]->ctx;
+            const auto t0 = std::chrono::steady_clock::now();
+            if (cudaSetDevice(c->device) != cudaSuccess) {
+                c->err = "picard_solve_batched: cannot make the context's device current";
+                status[i] = TT_ECUDA;
+                return;
+            }
+            status[i] = picard_solve(c, probs[i], &opts[i], &u[i], &p[i], &stats[i]);
+            cudaStreamSynchronize(c->stream);
+            if (seconds) seconds[i] = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        });
+    }
+    for (auto& w : workers) w.join();
+    for (int i = 0; i < nprob; ++i)
+        if (status[i] != TT_OK) return status[i];
+    return TT_OK;
 }
 
 }  // extern "C"

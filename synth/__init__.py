@@ -7,4 +7,4 @@ None of these modules holds solver arithmetic.
 from .mesh import Mesh, step_mesh, channel_mesh
 from .kl import viscosity_fields, kl_eigenpairs
 from .problem import (Problem, Tolerances, gpc_multi_indices, n_xi, make_problem,
-                      preset, random_tt, time_profile)
+                      preset, random_tt, time_profile, batch)

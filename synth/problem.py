@@ -136,6 +136,20 @@ def preset(name: str, **over) -> Problem:
     return make_problem(name, **kw)
 
 
+def batch(name: str, count: int, seed: int = 5, nu0_range=(1 / 200, 1 / 50), sigma_range=(0.05, 0.3),
+          **over) -> list:
+    """`count` independent problems of preset `name` with seeded draws of the
+    viscosity: nu0 log-uniform in nu0_range, sigma uniform in sigma_range."""
+    rng = np.random.default_rng(seed)
+    lo, hi = np.log(nu0_range[0]), np.log(nu0_range[1])
+    out = []
+    for _ in range(count):
+        nu0 = float(np.exp(rng.uniform(lo, hi)))
+        sigma = float(rng.uniform(*sigma_range))
+        out.append(preset(name, nu0=nu0, sigma=sigma, **over))
+    return out
+
+
 def random_tt(n_t, n_xi_, n_x, r1, r2, seed=0, decay=None):
     """Seeded random TT cores in the paper's shapes (n_t x r1, r1 x n_xi x r2, r2 x n_x).
 

@@ -200,3 +200,13 @@ def test_grouped_convection_equals_term_by_term_sum(tiny, mean):
     literal = add(*[(1.0, t) for t in d.conv_terms(w, u, mean=mean)])
     assert grouped.ranks == (2 * u.ranks[0], 3 * u.ranks[1])
     assert np.abs(grouped.vec() - literal.vec()).max() < 1e-12 * np.abs(literal.vec()).max()
+
+
+def test_batch_generator_is_seeded_and_within_ranges():
+    import synth
+    a = synth.batch("tiny", 4, seed=9, nu0_range=(1 / 200, 1 / 50), sigma_range=(0.05, 0.3))
+    b = synth.batch("tiny", 4, seed=9, nu0_range=(1 / 200, 1 / 50), sigma_range=(0.05, 0.3))
+    for x, y in zip(a, b):
+        assert x.params["nu0"] == y.params["nu0"] and x.params["sigma"] == y.params["sigma"]
+        assert 1 / 200 <= x.params["nu0"] <= 1 / 50 and 0.05 <= x.params["sigma"] <= 0.3
+    assert len({x.params["nu0"] for x in a}) == 4
