@@ -461,6 +461,54 @@ __device__ __forceinline__ bool jacobi_pair(T* ca, T* cb, int a, int b, int m, i
     return true;
 }
 
+// Same rotation for m <= 32 KV rows (and no extra rows), with each lane's share of
+// both columns held in registers between the dot product and the rotation, so the
+// pair is read from L2 once.  The arithmetic and its order are those of
+// jacobi_pair (rows past m contribute exact zeros).
+template <typename T, int KV>
+__device__ __forceinline__ bool jacobi_pair_reg(T* ca, T* cb, int a, int b, int m, T* dn, T tol, T tiny,
+                                                double& flops) {
+    const int lane = threadIdx.x & 31;
+    const T al = __ldcg(dn + a), be = __ldcg(dn + b);
+    T xa[KV], xb[KV];
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+        const int i = lane + 32 * k;
+        xa[k] = i < m ? __ldcg(ca + i) : T(0);
+        xb[k] = i < m ? __ldcg(cb + i) : T(0);
+    }
+    T ga = T(0);
+#pragma unroll
+    for (int k = 0; k < KV; ++k)
+        if (lane + 32 * k < m) ga = fma(xa[k], xb[k], ga);
+    ga = warp_sum(ga);
+    flops += 2.0 * m;
+    if (!(al > tiny && be > tiny && fabs(ga) > tol * sqrt(al) * sqrt(be))) return false;
+    const T zeta = (be - al) / (T(2) * ga);
+    const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+    const T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
+    T na = T(0), nb = T(0);
+#pragma unroll
+    for (int k = 0; k < KV; ++k) {
+        const int i = lane + 32 * k;
+        if (i < m) {
+            const T xn = cs * xa[k] - sn * xb[k], yn = sn * xa[k] + cs * xb[k];
+            ca[i] = xn;
+            cb[i] = yn;
+            na = fma(xn, xn, na);
+            nb = fma(yn, yn, nb);
+        }
+    }
+    na = warp_sum(na);
+    nb = warp_sum(nb);
+    if (lane == 0) {
+        dn[a] = na;
+        dn[b] = nb;
+    }
+    flops += 10.0 * m;
+    return true;
+}
+
 // Round-robin (circle) pairing: round r pairs (r, npad-1) and ((r+p) mod (npad-1),
 // (r-p) mod (npad-1)) for p = 1 .. npad/2-1; a column index >= n is a dummy.
 __device__ __forceinline__ void circle_pair(int r, int p, int NR, int& a, int& b) {
@@ -499,9 +547,13 @@ k_jacobi(int m, int mr, int n, int npad, T* W, int ldw, int* flags, int max_swee
                 int a, b;
                 circle_pair(r, p, NR, a, b);
                 if (a >= n || b >= n) continue;
-                if (jacobi_pair<T, true>(W + (size_t)a * ldw, W + (size_t)b * ldw, a, b, m, mr, dn, tol, tiny,
-                                         myflops))
-                    any = 1;
+                T* ca = W + (size_t)a * ldw;
+                T* cb = W + (size_t)b * ldw;
+                bool rot;
+                if (mr == m && m <= 128) rot = jacobi_pair_reg<T, 4>(ca, cb, a, b, m, dn, tol, tiny, myflops);
+                else if (mr == m && m <= 256) rot = jacobi_pair_reg<T, 8>(ca, cb, a, b, m, dn, tol, tiny, myflops);
+                else rot = jacobi_pair<T, true>(ca, cb, a, b, m, mr, dn, tol, tiny, myflops);
+                if (rot) any = 1;
             }
             group_barrier<kCluster>(bar, gridDim.x, status);
         }
