@@ -5,7 +5,7 @@ Oracle (test infrastructure only; see oracle/__init__.py).
 
 Vectors are either single TTs (inner solve) or (velocity TT, pressure TT)
 pairs (outer solve); the pair's TTs are truncated separately (Section 4.2).
-Fixed choices where the paper leaves room (listed in the design doc as readings):
+Fixed choices where the paper leaves room (the GPU path makes the same ones):
 z_0 = 0, no restarts, modified Gram-Schmidt without intermediate truncation,
 h_{k+1,k} = ||x|| from the orthogonalised train and v_{k+1} = T(x)/h (T is
 scale-equivariant), the stopping test on the norm of the truncated s_k, happy
