@@ -11,6 +11,8 @@ Modules and the passages they follow:
   tt      tensor trains, eq. (z_tt), eq. (Xz), Algorithm 4.1, truncation (Section 4.1)
   system  the all-at-once operator, eq. (F), eq. (ns_sys_all), eq. (N_kron)
   solver  Algorithm 4.2, eq. (mean_lsc), eq. (11_prec), Algorithm 3.1
+  learned the learned replacement of K^{-1} in eq. (11_prec) (no counterpart in
+          the paper): conv net forward/backward, loss, Adam, training pairs
 
 Every function is pinned by a `-m "not gpu"` test to something other than
 itself (closed forms, exactly representable solutions, a sparse direct solve

@@ -106,6 +106,27 @@ def gmres(apply_L, apply_P, b, *, tol, eps, maxit, space, bnorm=None, log=None):
 
 
 # ---------------------------------------------------------------- preconditioner
+def mean_velocity_field(w):
+    """Time average of the mean (psi_1) mode of the full-node convection TT w:
+    the field w_avg of eq. (11_prec), as a (2 n_nodes,) vector."""
+    c = w.z1.mean(axis=0) @ w.z2[:, 0, :]
+    return c @ w.z3
+
+
+def mean_oseen_matrix(disc, w):
+    """K = tau^-1 M + A_0 + N(w_avg) over the free scalar velocity dofs, the
+    spatial factor of eq. (11_prec) (w None: no convection)."""
+    d = disc
+    K = d.M / d.tau + d.A[0]
+    if w is not None:
+        wavg = mean_velocity_field(w)
+        n = d.n_nodes
+        from . import fem
+        Nf = fem.convection(d.prob.mesh, wavg[:n], wavg[n:])
+        K = K + Nf[d.free][:, d.free]
+    return sp.csc_matrix(K)
+
+
 class MeanLSC:
     """Mean-based block triangular preconditioner (eq. prec) with S^{-1} from
     eq. (mean_lsc) and the (1,1) solve by an inner low-rank GMRES preconditioned
@@ -114,23 +135,18 @@ class MeanLSC:
     w: the (truncated) full-node convection TT, or None for the Stokes problem.
     """
 
-    def __init__(self, disc, w, eps, tol_inner, maxit_inner):
+    def __init__(self, disc, w, eps, tol_inner, maxit_inner, learned_minv=None):
         self.d, self.w, self.eps = disc, w, eps
+        # optional replacement of M^{-1} in the inner solve (a learned K^{-1}); the
+        # exact M^{-1} is the fallback when the inner solve misses its tolerance with it
+        self.learned_minv = learned_minv
+        self.fallbacks = 0
         self.tol_inner, self.maxit_inner = tol_inner, maxit_inner
         d = disc
         self.Minv = sp.diags(1.0 / d.Mstar_diag)
         Lp = (d.B @ self.Minv @ d.Bt).tocsc()                    # B M_*^{-1} B^T
         self.Lp = spla.splu(Lp)
-        K = d.M / d.tau + d.A[0]
-        if w is not None:
-            # w_avg: time average of the mean (psi_1) mode of w (Section 5.3)
-            c = w.z1.mean(axis=0) @ w.z2[:, 0, :]                # (k2,)
-            wavg = c @ w.z3                                        # full-node field
-            n = d.n_nodes
-            from . import fem
-            Nf = fem.convection(d.prob.mesh, wavg[:n], wavg[n:])
-            K = K + Nf[d.free][:, d.free]
-        self.K = spla.splu(sp.csc_matrix(K))
+        self.K = spla.splu(mean_oseen_matrix(d, w))
         n_t = d.n_t
         self.cum = np.tril(np.ones((n_t, n_t)))                  # (I - C)^{-1}
         self.inner_its = []
@@ -163,8 +179,16 @@ class MeanLSC:
         d = self.d
         p = self.schur(ap)
         rhs, _ = round_tt(add((1.0, au), (-1.0, kron_apply(None, None, d.Bt, p))), self.eps)
-        u, st = gmres(lambda z: d.apply_mean(self.w, z), self.apply_Minv, rhs,
-                      tol=self.tol_inner, eps=self.eps, maxit=self.maxit_inner, space=_Single)
+        A = lambda z: d.apply_mean(self.w, z)
+        if self.learned_minv is not None:
+            u, st = gmres(A, self.learned_minv, rhs, tol=self.tol_inner, eps=self.eps,
+                          maxit=self.maxit_inner, space=_Single)
+            if st["res"][-1] <= self.tol_inner * st["bnorm"]:
+                self.inner_its.append(st["its"])
+                return (u, p)
+            self.fallbacks += 1
+        u, st = gmres(A, self.apply_Minv, rhs, tol=self.tol_inner, eps=self.eps,
+                      maxit=self.maxit_inner, space=_Single)
         self.inner_its.append(st["its"])
         return (u, p)
 
