@@ -203,7 +203,7 @@ def run_ours(a):
     stream = torch.cuda.current_stream()
 
     def timed(mixed, profile):
-        opts = binding.opts_from(prob.tol, mixed=mixed)
+        opts = binding.opts_from(prob.tol, precision=mixed)
         last = None
         for _ in range(a.warmup):
             last = P.picard(opts)
@@ -333,7 +333,7 @@ def run_batch(a):
     ctxs = [binding.Context(stream=s.cuda_stream) for s in streams]
     handles = [c.problem(pr) for c, pr in zip(ctxs, probs)]
     mixed = 1 if a.precision == "mixed" else 0
-    opts = [binding.opts_from(pr.tol, mixed=mixed) for pr in probs]
+    opts = [binding.opts_from(pr.tol, precision=mixed) for pr in probs]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     for _ in range(a.warmup):
         binding.picard_batched(handles, opts)

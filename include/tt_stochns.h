@@ -27,6 +27,8 @@
 #ifndef TT_STOCHNS_H
 #define TT_STOCHNS_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -46,12 +48,27 @@ typedef struct tt_ctx tt_ctx;
 typedef struct tt_t tt_t;
 typedef struct tt_problem tt_problem;
 typedef struct tt_op tt_op;
+typedef struct tt_prec tt_prec;
+typedef struct tt_net tt_net;
+
+/* Caller-supplied device allocator (for example a framework's caching allocator).
+ * alloc returns `bytes` of device memory usable in stream order on `stream` (a
+ * cudaStream_t), or NULL on failure (the call then fails with TT_ENOMEM); free
+ * releases a block alloc returned, with the same size, in stream order.  `user`
+ * is passed through unchanged.  The callbacks may be called from any thread that
+ * calls into the library. */
+typedef void* (*tt_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*tt_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
 
 /* ---- context ------------------------------------------------------------ */
 
 /* Create a context on the current CUDA device.  cuda_stream: a cudaStream_t
- * (NULL = the legacy default stream) on which all work of this context runs. */
-int tt_ctx_create(void* cuda_stream, tt_ctx** out);
+ * (NULL = the legacy default stream) on which all work of this context runs.
+ * alloc, free: device memory for every train and every work buffer of this
+ * context; both NULL = the library's own stream-ordered pool (cudaMallocAsync).
+ * Passing only one of the two is TT_EINVAL.  A few bytes of bookkeeping (status
+ * word, barrier counters, pinned staging) are allocated by the library itself. */
+int tt_ctx_create(void* cuda_stream, tt_alloc_fn alloc, tt_free_fn free, void* user, tt_ctx** out);
 int tt_ctx_destroy(tt_ctx* ctx);
 /* Message of the last failure in this context (static storage, never NULL). */
 const char* tt_last_error(const tt_ctx* ctx);
@@ -71,13 +88,18 @@ int tt_ctx_prof_read(tt_ctx* ctx, int slot, long long* launches, double* ms, dou
 
 /* ---- tensor trains (Section 4.1) ------------------------------------------ */
 
-/* Copy cores (layout above) into a new device-resident train.
+enum { TT_F64 = 0 };   /* storage type of train cores (FP64 is the only one) */
+
+/* Copy cores (layout above) into a new device-resident train of ranks (r1, r2)
+ * whose allocation can hold ranks up to (rcap1, rcap2) (rcap <= 0: equal to the
+ * rank; rcap < rank is TT_EINVAL).  dtype: TT_F64.
  * src_on_device: 0 = the three pointers are host memory, 1 = device memory. */
-int tt_create(tt_ctx* ctx, int n_t, int n_xi, int n_x, int r1, int r2,
-              const double* z1, const double* z2, const double* z3,
-              int src_on_device, tt_t** out);
+int tt_create(tt_ctx* ctx, int n_t, int n_xi, int n_x, int r1, int r2, int rcap1, int rcap2, int dtype,
+              const double* z1, const double* z2, const double* z3, int src_on_device, tt_t** out);
 int tt_destroy(tt_t* t);
 int tt_shape(const tt_t* t, int* n_t, int* n_xi, int* n_x, int* r1, int* r2);
+/* Rank capacities of the train's allocation. */
+int tt_capacity(const tt_t* t, int* rcap1, int* rcap2);
 /* Copy the cores out (buffers sized from tt_shape). */
 int tt_get_cores(tt_ctx* ctx, const tt_t* t, double* z1, double* z2, double* z3,
                  int dst_on_device);
@@ -90,11 +112,24 @@ int tt_get_cores(tt_ctx* ctx, const tt_t* t, double* z1, double* z2, double* z3,
 int tt_round(tt_ctx* ctx, const tt_t* in, double eps, tt_t** out,
              double* norm_before, double* norm_after);
 
+/* T_eps(in) written into the existing train `out` (same mode sizes), within its
+ * rank capacities.  If a rank of T_eps(in) exceeds out's capacity, out holds the
+ * truncation to the capacity (the leading singular triplets of each unfolding;
+ * the eps bound then does not hold) and the call returns TT_ERANK.  `in` and
+ * `out` may not be the same train. */
+int tt_round_to(tt_ctx* ctx, const tt_t* in, double eps, tt_t* out, double* norm_before,
+                double* norm_after);
+
 /* <vec a, vec b> (Section 4.1) into *out (host). */
 int tt_dot(tt_ctx* ctx, const tt_t* a, const tt_t* b, double* out);
 
-/* alpha a + beta b by concatenating cores (ranks add; no truncation). */
-int tt_axpby(tt_ctx* ctx, double alpha, const tt_t* a, double beta, const tt_t* b,
+/* ||vec a||_F into *out (host): the square root of <a, a> by the same core
+ * contractions as tt_dot. */
+int tt_norm(tt_ctx* ctx, const tt_t* a, double* out);
+
+/* alpha a + beta b by concatenating cores (ranks add, Section 4.1); eps > 0 then
+ * truncates the sum with T_eps, eps <= 0 returns it untruncated. */
+int tt_axpby(tt_ctx* ctx, double alpha, const tt_t* a, double beta, const tt_t* b, double eps,
              tt_t** out);
 
 /* <vec a, vec b> into *out (host), like tt_dot, for callers that cannot allocate
@@ -177,11 +212,88 @@ int tt_op_destroy(tt_op* op);
 int tt_matvec(tt_ctx* ctx, const tt_op* op, const tt_t* u, const tt_t* p, double eps,
               tt_t** out_u, tt_t** out_p);
 
-/* Mean-based block triangular preconditioner of eq. (prec) with the LSC Schur
- * approximation of eq. (mean_lsc) and the inner low-rank GMRES solve of
- * eq. (11_sys) preconditioned by eq. (11_prec), applied to (a_u, a_p). */
-int tt_prec_apply(tt_ctx* ctx, tt_op* op, const tt_t* au, const tt_t* ap, double eps,
-                  double tol_inner, int maxit_inner, tt_t** u, tt_t** p, int* inner_its);
+/* ---- preconditioners (eq. prec, Section 5) ---------------------------------- */
+
+enum {
+    TT_PREC_LSC = 0,      /* mean-based LSC Schur approximation, eq. (mean_lsc), with the
+                             (1,1) block solved by inner low-rank GMRES on eq. (11_sys)
+                             preconditioned by eq. (11_prec) */
+    TT_PREC_LEARNED = 1,  /* the same, with the spatial factor K^-1 of eq. (11_prec)
+                             replaced by a trained network (tt_net); an inner solve that
+                             misses tol_inner with it is redone with the exact K^-1 */
+    TT_PREC_PCD = 2       /* mean-based PCD, eq. (mean_pcd): not built (TT_EINVAL) */
+};
+
+typedef struct {
+    double eps;           /* truncation inside the preconditioner (the LSC product, the
+                             inner GMRES) */
+    double tol_inner;     /* inner solve stopping ||y - (F_0 + C) v|| <= tol_inner ||y|| */
+    int maxit_inner;      /* inner GMRES iteration cap (<= 63) */
+    const tt_net* net;    /* TT_PREC_LEARNED: the network (kept by reference; it must
+                             outlive the preconditioner); NULL otherwise */
+} tt_prec_opts;
+
+/* Preconditioner of the given kind for a FULL operator (its convection field). */
+int tt_prec_create(tt_ctx* ctx, tt_op* op, int kind, const tt_prec_opts* opts, tt_prec** out);
+int tt_prec_destroy(tt_prec* prec);
+
+/* Block triangular preconditioner of eq. (prec): p = -S^-1 a_p,
+ * u = (F_0 + C)^-1 (a_u - B^T p), applied to (a_u, a_p).  inner_its: iterations of
+ * the inner solve(s); fallbacks: learned inner solves redone with the exact K^-1
+ * (either pointer may be NULL). */
+int tt_prec_apply(tt_ctx* ctx, tt_prec* prec, const tt_t* au, const tt_t* ap, tt_t** u, tt_t** p,
+                  int* inner_its, int* fallbacks);
+
+/* ---- learned mean-Oseen solve (no counterpart in the paper) ------------------ */
+
+/* A convolutional network Phi that approximates K^-1 r for the spatial factor
+ * K = tau^-1 M + A_0 + N(w_avg) of eq. (11_prec), on the lattice of the problem's
+ * velocity nodes (spacing h/2 over the bounding box).  Layers: `depth` 3x3
+ * convolutions with zero padding, channels 5 -> C -> ... -> C -> 2, ReLU after all
+ * but the last.  Input channels: the two residual components divided by the
+ * residual's norm s, the two components of w_avg, the domain mask; output: the two
+ * correction components at the free nodes, multiplied by s.  Weights are kept in
+ * FP32 and used in BF16; products accumulate in FP32.
+ * params (host, FP32): per layer l its weights W_l[out][in][3][3] then its biases
+ * b_l[out], layers in order (tt_net_info gives the count).  The network belongs to
+ * the problem's mesh; its buffers come from ctx, which must outlive it. */
+int tt_net_create(tt_ctx* ctx, const tt_problem* prob, int channels, int depth, const float* params,
+                  tt_net** out);
+int tt_net_destroy(tt_net* net);
+int tt_net_info(const tt_net* net, int* nparams, int* nx, int* ny);
+/* Current FP32 parameters (layout as in tt_net_create) into params (host). */
+int tt_net_get_params(tt_ctx* ctx, const tt_net* net, float* params);
+
+/* Residual blocks R (and targets T) are n_u x count, row-major (element (i, b) at
+ * i * count + b, rows in the velocity order of the trains), host memory
+ * (on_device = 0) or device memory (1).  w_avg comes from the operator's
+ * convection field (zero for a Stokes operator). */
+
+/* out = Phi(r_b) for every column b (same layout as R). */
+int tt_net_apply(tt_ctx* ctx, const tt_net* net, const tt_op* op, const double* R, int count, int on_device,
+                 double* out);
+/* Training loss (1/count) sum_b ||Phi(r_b) - t_b||^2 / ||t_b||^2 and its gradient with
+ * respect to the parameters (host FP32, layout of tt_net_create; may be NULL),
+ * without changing the network. */
+int tt_net_loss_grad(tt_ctx* ctx, tt_net* net, const tt_op* op, const double* R, const double* T, int count,
+                     int on_device, double* loss, float* grads);
+
+typedef struct {
+    int epochs;          /* passes over the pairs */
+    int batch;           /* pairs per Adam step (a trailing partial batch is skipped) */
+    float lr;            /* Adam step size (beta1 0.9, beta2 0.999, eps 1e-8) */
+    int smooth_max;      /* residual group g of smooth_max + 1 equal contiguous groups gets g
+                            weighted-Jacobi sweeps r <- r - omega D^-1 K r before its target */
+    float omega;
+} tt_train_opts;
+
+/* Train the network on the pairs (r_b, K^-1 r_b): the residuals R are first
+ * smoothed (tt_train_opts), the targets come from the exact banded solve with the
+ * operator's K (FP64); then `epochs` passes of Adam steps over consecutive batches
+ * in the given order.  epoch_loss (host, `epochs` values, may be NULL): mean batch
+ * loss of every pass. */
+int tt_net_train(tt_ctx* ctx, tt_net* net, tt_op* op, const double* R, int count, int on_device,
+                 const tt_train_opts* opts, double* epoch_loss);
 
 /* Nonlinear residual r = f - A(w)[u; p], w = E u + u_D untruncated
  * (Section 4.3), truncated with eps; *norm = ||T(r)||. */
@@ -189,6 +301,8 @@ int tt_residual(tt_ctx* ctx, tt_problem* prob, const tt_t* u, const tt_t* p, dou
                 tt_t** ru, tt_t** rp, double* norm);
 
 /* ---- solvers (Algorithms 4.2, 3.1) ----------------------------------------- */
+
+enum { TT_FP64 = 0, TT_MIXED = 1 };
 
 typedef struct {
     double tol_picard;   /* Picard stopping ||r|| <= tol_picard ||f|| */
@@ -198,12 +312,17 @@ typedef struct {
     double eps_conv;     /* truncation of the convection field, eq. (eps_conv) */
     double tol_inner;    /* inner (F_0 + C) solve stopping, Section 5.3 */
     int maxit_picard, maxit_gmres, maxit_inner;
-    int mixed;           /* 0: FP64 throughout; 1: inside GMRES (matvecs, truncations, the
-                            preconditioner) SpMM, GEMM, Householder R factors and banded
-                            solves compute in FP32 on FP64-stored trains, while inner
-                            products, Hessenberg least squares, the SVDs of the
-                            truncations, band factorisations, the Picard residual and the
-                            Picard-level truncations stay FP64 */
+    int precision;       /* TT_FP64: FP64 throughout; TT_MIXED: inside GMRES (matvecs,
+                            truncations, the preconditioner) SpMM, GEMM, Householder R
+                            factors and banded solves compute in FP32 on FP64-stored
+                            trains, while inner products, Hessenberg least squares, the
+                            SVDs of the truncations, band factorisations, the Picard
+                            residual and the Picard-level truncations stay FP64 */
+    const tt_net* learned;  /* non-NULL: TT_PREC_LEARNED preconditioner with this network
+                               at every Picard step (exact fallback); NULL: TT_PREC_LSC */
+    const tt_t* init_u;     /* non-NULL (with init_p): start Algorithm 3.1 from this
+                               iterate instead of the Stokes solve (resume a solve) */
+    const tt_t* init_p;
 } tt_solver_opts;
 
 typedef struct {
@@ -211,6 +330,7 @@ typedef struct {
     double res0;         /* ||s_0|| */
     double res;          /* ||s_k|| at exit */
     int inner_its;       /* total inner iterations of the preconditioner */
+    int fallbacks;       /* learned inner solves redone with the exact K^-1 */
 } tt_gmres_stats;
 
 #define TT_MAX_PICARD 64
@@ -223,18 +343,20 @@ typedef struct {
     int inner_its[TT_MAX_PICARD + 1];
     int ranks[TT_MAX_PICARD + 1][4];      /* u (k1,k2), p (k1,k2) after each step */
     int conv_ranks[TT_MAX_PICARD + 1][2]; /* truncated convection field */
+    int fallbacks[TT_MAX_PICARD + 1];     /* learned inner solves redone exactly */
 } tt_picard_stats;
 
 /* Low-rank flexible GMRES (Algorithm 4.2) for op [z_u; z_p] = [b_u; b_p] with
- * the preconditioner above, z_0 = 0, stop when ||s_k|| <= tol_gmres * bnorm
- * (bnorm <= 0: use ||b||).  Returns TT_ENOCONV (with the last iterate) if
- * maxit_gmres is reached first. */
-int tt_gmres(tt_ctx* ctx, tt_op* op, const tt_solver_opts* opts, const tt_t* bu,
+ * the preconditioner prec (NULL: TT_PREC_LSC built from opts), z_0 = 0, stop
+ * when ||s_k|| <= tol_gmres * bnorm (bnorm <= 0: use ||b||).  Returns
+ * TT_ENOCONV (with the last iterate) if maxit_gmres is reached first. */
+int tt_gmres(tt_ctx* ctx, tt_op* op, tt_prec* prec, const tt_solver_opts* opts, const tt_t* bu,
              const tt_t* bp, double bnorm, tt_t** zu, tt_t** zp, tt_gmres_stats* stats);
 
 /* Truncated inexact Picard iteration (Algorithm 3.1, eq. eps_soln, eq. eps_conv,
- * Section 5.2): Stokes initial iterate, then correction solves until
- * ||r|| <= tol_picard ||f||.  Returns the velocity and pressure trains. */
+ * Section 5.2): Stokes initial iterate (or opts->init_u, init_p), then correction
+ * solves until ||r|| <= tol_picard ||f||.  Returns the velocity and pressure
+ * trains; stats index 0 is the Stokes solve (zero when resumed). */
 int picard_solve(tt_ctx* ctx, tt_problem* prob, const tt_solver_opts* opts, tt_t** u,
                  tt_t** p, tt_picard_stats* stats);
 

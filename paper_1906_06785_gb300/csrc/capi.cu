@@ -1,5 +1,6 @@
 // extern "C" entry points declared in include/tt_stochns.h.  Every entry point
 // catches the library's exceptions and turns them into status codes.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <map>
@@ -98,6 +99,15 @@ void prof_resolve(tt_ctx* c) {
 }
 }  // namespace tt
 
+// A preconditioner object: the kind and options, applied through LSCPrec.
+struct tt_prec {
+    tt_ctx* c = nullptr;
+    tt_op* op = nullptr;
+    int kind = TT_PREC_LSC;
+    tt_prec_opts o{};
+    LSCPrec make() const { return LSCPrec{c, op, o.eps, o.tol_inner, o.maxit_inner, o.net}; }
+};
+
 #define API_BEGIN(ctx) \
     tt_ctx* _ctx = (ctx); \
     try {
@@ -115,12 +125,16 @@ void prof_resolve(tt_ctx* c) {
 
 extern "C" {
 
-int tt_ctx_create(void* stream, tt_ctx** out) {
+int tt_ctx_create(void* stream, tt_alloc_fn alloc, tt_free_fn free_fn, void* user, tt_ctx** out) {
     if (!out) return TT_EINVAL;
     *out = nullptr;
+    if ((alloc == nullptr) != (free_fn == nullptr)) return TT_EINVAL;
     tt_ctx* c = new tt_ctx;
     try {
         c->stream = (cudaStream_t)stream;
+        c->alloc_fn = alloc;
+        c->free_fn = free_fn;
+        c->alloc_user = user;
         CUDA_CHECK(cudaGetDevice(&c->device));
         CUDA_CHECK(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device));
         int coop = 0;
@@ -191,12 +205,13 @@ int tt_ctx_prof_read(tt_ctx* ctx, int slot, long long* n, double* ms, double* fl
     API_END
 }
 
-int tt_create(tt_ctx* ctx, int n_t, int n_xi, int n_x, int r1, int r2, const double* z1, const double* z2,
-              const double* z3, int src_on_device, tt_t** out) {
+int tt_create(tt_ctx* ctx, int n_t, int n_xi, int n_x, int r1, int r2, int rcap1, int rcap2, int dtype,
+              const double* z1, const double* z2, const double* z3, int src_on_device, tt_t** out) {
     API_BEGIN(ctx)
     TT_REQUIRE(ctx && out && z1 && z2 && z3, "null argument");
+    TT_REQUIRE(dtype == TT_F64, "unsupported train dtype %d (TT_F64 only)", dtype);
     *out = nullptr;
-    TTPtr t = wrap(tt_alloc(ctx, n_t, n_xi, n_x, r1, r2));
+    TTPtr t = wrap(tt_alloc(ctx, n_t, n_xi, n_x, r1, r2, rcap1, rcap2));
     const cudaMemcpyKind k = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     CUDA_CHECK(cudaMemcpyAsync(t->z1, z1, (size_t)n_t * r1 * sizeof(double), k, ctx->stream));
     CUDA_CHECK(cudaMemcpyAsync(t->z2, z2, (size_t)r1 * n_xi * r2 * sizeof(double), k, ctx->stream));
@@ -222,6 +237,13 @@ int tt_shape(const tt_t* t, int* n_t, int* n_xi, int* n_x, int* r1, int* r2) {
     return TT_OK;
 }
 
+int tt_capacity(const tt_t* t, int* rcap1, int* rcap2) {
+    if (!t) return TT_EINVAL;
+    if (rcap1) *rcap1 = t->cap1;
+    if (rcap2) *rcap2 = t->cap2;
+    return TT_OK;
+}
+
 int tt_get_cores(tt_ctx* ctx, const tt_t* t, double* z1, double* z2, double* z3, int dst_on_device) {
     API_BEGIN(ctx)
     TT_REQUIRE(ctx && t, "null argument");
@@ -244,6 +266,25 @@ int tt_round(tt_ctx* ctx, const tt_t* in, double eps, tt_t** out, double* nb, do
     API_END
 }
 
+int tt_round_to(tt_ctx* ctx, const tt_t* in, double eps, tt_t* out, double* nb, double* na) {
+    API_BEGIN(ctx)
+    TT_REQUIRE(ctx && in && out, "null argument");
+    TT_REQUIRE(in != out, "tt_round_to: input and output are the same train");
+    TT_REQUIRE(in->n_t == out->n_t && in->n_xi == out->n_xi && in->n_x == out->n_x,
+               "tt_round_to: mode sizes differ");
+    RoundOut info;
+    TTPtr r = round_tt(ctx, in, eps, &info, out->cap1, out->cap2);
+    copy_cores(ctx, r.get(), out);
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    if (nb) *nb = info.nrm_before;
+    if (na) *na = info.nrm_after;
+    if (info.capped) {
+        ctx->err = "tt_round_to: a rank of the truncation exceeds the output capacity; output truncated to it";
+        return TT_ERANK;
+    }
+    API_END
+}
+
 int tt_dot(tt_ctx* ctx, const tt_t* a, const tt_t* b, double* out) {
     API_BEGIN(ctx)
     TT_REQUIRE(ctx && a && b && out, "null argument");
@@ -251,10 +292,21 @@ int tt_dot(tt_ctx* ctx, const tt_t* a, const tt_t* b, double* out) {
     API_END
 }
 
-int tt_axpby(tt_ctx* ctx, double alpha, const tt_t* a, double beta, const tt_t* b, tt_t** out) {
+int tt_norm(tt_ctx* ctx, const tt_t* a, double* out) {
+    API_BEGIN(ctx)
+    TT_REQUIRE(ctx && a && out, "null argument");
+    const double d = dot_host(ctx, a, a);
+    if (!(d == d) || std::isinf(d)) TT_THROW(TT_ENAN, "non-finite norm");
+    *out = std::sqrt(std::max(d, 0.0));
+    API_END
+}
+
+int tt_axpby(tt_ctx* ctx, double alpha, const tt_t* a, double beta, const tt_t* b, double eps, tt_t** out) {
     API_BEGIN(ctx)
     TT_REQUIRE(ctx && a && b && out, "null argument");
-    *out = concat(ctx, {Summand{alpha, nullptr, a}, Summand{beta, nullptr, b}}).release();
+    TTPtr s = concat(ctx, {Summand{alpha, nullptr, a}, Summand{beta, nullptr, b}});
+    if (eps > 0.0) s = round_tt(ctx, s.get(), eps);
+    *out = s.release();
     API_END
 }
 
@@ -367,16 +419,42 @@ int tt_matvec(tt_ctx* ctx, const tt_op* op, const tt_t* u, const tt_t* p, double
     API_END
 }
 
-int tt_prec_apply(tt_ctx* ctx, tt_op* op, const tt_t* au, const tt_t* ap, double eps, double tol_inner,
-                  int maxit_inner, tt_t** u, tt_t** p, int* inner_its) {
+int tt_prec_create(tt_ctx* ctx, tt_op* op, int kind, const tt_prec_opts* o, tt_prec** out) {
     API_BEGIN(ctx)
-    TT_REQUIRE(ctx && op && au && ap && u && p, "null argument");
-    LSCPrec pre{ctx, op, eps, tol_inner, maxit_inner};
+    TT_REQUIRE(ctx && op && o && out, "null argument");
+    *out = nullptr;
+    TT_REQUIRE(op->which == TT_OP_FULL, "a preconditioner needs a FULL operator");
+    TT_REQUIRE(o->maxit_inner >= 1 && o->maxit_inner <= 63, "maxit_inner must be in [1, 63]");
+    if (kind == TT_PREC_PCD) TT_THROW(TT_EINVAL, "the mean-based PCD preconditioner is not built");
+    TT_REQUIRE(kind == TT_PREC_LSC || kind == TT_PREC_LEARNED, "unknown preconditioner kind %d", kind);
+    TT_REQUIRE(kind == TT_PREC_LSC || o->net, "TT_PREC_LEARNED needs a network");
+    tt_prec* pr = new tt_prec;
+    pr->c = ctx;
+    pr->op = op;
+    pr->kind = kind;
+    pr->o = *o;
+    if (kind == TT_PREC_LSC) pr->o.net = nullptr;
+    *out = pr;
+    API_END
+}
+
+int tt_prec_destroy(tt_prec* prec) {
+    if (!prec) return TT_EINVAL;
+    delete prec;
+    return TT_OK;
+}
+
+int tt_prec_apply(tt_ctx* ctx, tt_prec* prec, const tt_t* au, const tt_t* ap, tt_t** u, tt_t** p, int* inner_its,
+                  int* fallbacks) {
+    API_BEGIN(ctx)
+    TT_REQUIRE(ctx && prec && au && ap && u && p, "null argument");
+    LSCPrec pre = prec->make();
     Vec v;
     v.u = clone(ctx, au);
     v.p = clone(ctx, ap);
     Vec r = pre.apply(v);
     if (inner_its) *inner_its = pre.inner_its;
+    if (fallbacks) *fallbacks = pre.fallbacks;
     *u = r.u.release();
     *p = r.p.release();
     CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
@@ -395,18 +473,20 @@ int tt_residual(tt_ctx* ctx, tt_problem* P, const tt_t* u, const tt_t* p, double
     API_END
 }
 
-int tt_gmres(tt_ctx* ctx, tt_op* op, const tt_solver_opts* o, const tt_t* bu, const tt_t* bp, double bnorm,
-             tt_t** zu, tt_t** zp, tt_gmres_stats* stats) {
+int tt_gmres(tt_ctx* ctx, tt_op* op, tt_prec* prec, const tt_solver_opts* o, const tt_t* bu, const tt_t* bp,
+             double bnorm, tt_t** zu, tt_t** zp, tt_gmres_stats* stats) {
     API_BEGIN(ctx)
     TT_REQUIRE(ctx && op && o && bu && bp && zu && zp, "null argument");
     TT_REQUIRE(op->which == TT_OP_FULL, "tt_gmres needs a FULL operator");
-    LSCPrec pre{ctx, op, o->eps_gmres, o->tol_inner, o->maxit_inner};
+    TT_REQUIRE(o->precision == TT_FP64 || o->precision == TT_MIXED, "unknown precision %d", o->precision);
+    TT_REQUIRE(!prec || prec->op == op, "the preconditioner belongs to another operator");
+    LSCPrec pre = prec ? prec->make() : LSCPrec{ctx, op, o->eps_gmres, o->tol_inner, o->maxit_inner, o->learned};
     Vec b;
     b.u = clone(ctx, bu);
     b.p = clone(ctx, bp);
     GmresOut go;
     tt_ctx* c = ctx;
-    PrecScope ps(ctx, o->mixed ? 1 : 0);
+    PrecScope ps(ctx, o->precision == TT_MIXED ? 1 : 0);
     Vec z = gmres(
         ctx, [c, op](const Vec& x) { Vec y; op_apply(c, op, x.u.get(), x.p.get(), &y.u, &y.p); return y; },
         [&pre](const Vec& v) { return pre.apply(v); }, b, o->tol_gmres, o->eps_gmres, o->maxit_gmres, bnorm, &go);
@@ -415,6 +495,7 @@ int tt_gmres(tt_ctx* ctx, tt_op* op, const tt_solver_opts* o, const tt_t* bu, co
         stats->res0 = go.res0;
         stats->res = go.res;
         stats->inner_its = pre.inner_its;
+        stats->fallbacks = pre.fallbacks;
     }
     *zu = z.u.release();
     *zp = z.p.release();

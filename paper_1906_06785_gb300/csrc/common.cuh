@@ -53,7 +53,7 @@ enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_NAN = 2 };
 // the algorithmic flops and bytes of every timed launch.
 enum ProfSlot : int {
     PROF_QR = 0, PROF_JACOBI, PROF_GEMM, PROF_SPMM, PROF_BAND_SOLVE, PROF_BAND_FACTOR,
-    PROF_CORE, PROF_ASSEMBLY, PROF_NSLOTS
+    PROF_CORE, PROF_ASSEMBLY, PROF_CONV, PROF_NSLOTS
 };
 struct ProfData {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[PROF_NSLOTS];
@@ -81,6 +81,11 @@ struct tt_ctx {
     int nsm = 0;
     long long launches = 0;
     std::string err = "ok";
+    // device memory: the caller's stream-ordered allocator when given, else the
+    // library's own cudaMallocAsync pool
+    tt_alloc_fn alloc_fn = nullptr;
+    tt_free_fn free_fn = nullptr;
+    void* alloc_user = nullptr;
     // small pinned host buffer for scalar read-back
     void* pinned = nullptr;
     // device status word (bounded waits) + barrier counters
@@ -93,6 +98,26 @@ namespace tt {
 
 inline void count_launch(tt_ctx* c, int n = 1) { c->launches += n; }
 
+// Device memory of the context: the caller's allocator when it gave one, else
+// the stream-ordered pool.  Both are ordered on the context stream.
+inline void* ctx_malloc(tt_ctx* c, size_t bytes) {
+    if (!bytes) return nullptr;
+    if (c->alloc_fn) {
+        void* p = c->alloc_fn(bytes, (void*)c->stream, c->alloc_user);
+        if (!p) TT_THROW(TT_ENOMEM, "caller allocator returned NULL for %zu bytes", bytes);
+        return p;
+    }
+    void* p = nullptr;
+    const cudaError_t e = cudaMallocAsync(&p, bytes, c->stream);
+    if (e != cudaSuccess) TT_THROW(TT_ENOMEM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    return p;
+}
+inline void ctx_free(tt_ctx* c, void* p, size_t bytes) {
+    if (!p) return;
+    if (c->free_fn) c->free_fn(p, bytes, (void*)c->stream, c->alloc_user);
+    else if (!c->alloc_fn) cudaFreeAsync(p, c->stream);
+}
+
 #define LAUNCH_CHECK(ctx)                                                         \
     do {                                                                          \
         ::tt::count_launch(ctx);                                                  \
@@ -101,32 +126,32 @@ inline void count_launch(tt_ctx* c, int n = 1) { c->launches += n; }
             TT_THROW(TT_ECUDA, "%s:%d launch: %s", __FILE__, __LINE__, cudaGetErrorString(_e)); \
     } while (0)
 
-// Stream-ordered device buffer (cudaMallocAsync pool on the context stream).
+// Stream-ordered device buffer from the context's allocator (ctx_malloc).
 template <typename T>
 struct DBuf {
     T* p = nullptr;
     size_t n = 0;
-    cudaStream_t s = nullptr;
+    tt_ctx* c = nullptr;
     DBuf() = default;
-    DBuf(tt_ctx* c, size_t count) { alloc(c, count); }
-    void alloc(tt_ctx* c, size_t count) {
+    DBuf(tt_ctx* ctx, size_t count) { alloc(ctx, count); }
+    void alloc(tt_ctx* ctx, size_t count) {
         release();
-        s = c->stream;
+        c = ctx;
         n = count;
-        if (count) CUDA_CHECK(cudaMallocAsync((void**)&p, count * sizeof(T), s));
+        p = static_cast<T*>(ctx_malloc(ctx, count * sizeof(T)));
     }
     void release() {
-        if (p) cudaFreeAsync(p, s);
+        if (p) ctx_free(c, p, n * sizeof(T));
         p = nullptr;
         n = 0;
     }
     ~DBuf() { release(); }
     DBuf(const DBuf&) = delete;
     DBuf& operator=(const DBuf&) = delete;
-    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; o.n = 0; }
+    DBuf(DBuf&& o) noexcept : p(o.p), n(o.n), c(o.c) { o.p = nullptr; o.n = 0; }
     DBuf& operator=(DBuf&& o) noexcept {
         release();
-        p = o.p; n = o.n; s = o.s;
+        p = o.p; n = o.n; c = o.c;
         o.p = nullptr; o.n = 0;
         return *this;
     }
@@ -176,6 +201,8 @@ struct PrecScope {
 struct tt_t {
     tt_ctx* ctx = nullptr;
     int n_t = 0, n_xi = 0, n_x = 0, r1 = 0, r2 = 0;
+    int cap1 = 0, cap2 = 0;   // rank capacities the allocation holds (>= r1, r2)
+    size_t bytes = 0;         // size of the allocation at base
     double* base = nullptr;
     double* z1 = nullptr;   // [r1][n_t]
     double* z2 = nullptr;   // [r1][n_xi][r2]
@@ -184,7 +211,8 @@ struct tt_t {
 
 namespace tt {
 
-tt_t* tt_alloc(tt_ctx* c, int n_t, int n_xi, int n_x, int r1, int r2);
+// New train; cap1, cap2 <= 0 mean capacities equal to the ranks.
+tt_t* tt_alloc(tt_ctx* c, int n_t, int n_xi, int n_x, int r1, int r2, int cap1 = 0, int cap2 = 0);
 void tt_free(tt_t* t);
 using TTPtr = std::unique_ptr<tt_t, void (*)(tt_t*)>;
 inline TTPtr wrap(tt_t* t) { return TTPtr(t, tt_free); }

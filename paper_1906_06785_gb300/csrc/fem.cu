@@ -402,15 +402,20 @@ void scatter_band(tt_ctx* c, tt_problem* P, const double* vals, double* ab) {
     LAUNCH_CHECK(c);
 }
 
-void assemble_K_band(tt_ctx* c, tt_problem* P, const double* wfield, double* ab) {
+void assemble_K_vals(tt_ctx* c, tt_problem* P, const double* wfield, double* kv) {
     const int nnz = P->ff.nnz;
-    DBuf<double> nv, kv(c, nnz);
+    DBuf<double> nv;
     if (wfield) {
         nv.alloc(c, nnz);
         assemble_conv(c, P, wfield, 1, 1, nv.p, nullptr);
     }
-    k_axpy3<<<ceil_div(nnz, 256), 256, 0, c->stream>>>(nnz, 1.0 / P->tau, P->M_ff.p, P->A_ff.p, nv.p, kv.p);
+    k_axpy3<<<ceil_div(nnz, 256), 256, 0, c->stream>>>(nnz, 1.0 / P->tau, P->M_ff.p, P->A_ff.p, nv.p, kv);
     LAUNCH_CHECK(c);
+}
+
+void assemble_K_band(tt_ctx* c, tt_problem* P, const double* wfield, double* ab) {
+    DBuf<double> kv(c, P->ff.nnz);
+    assemble_K_vals(c, P, wfield, kv.p);
     fill_zero(c, ab, (size_t)P->n_v * (2 * P->bwK + 1));
     scatter_band(c, P, kv.p, ab);
     band_factor(c, ab, P->n_v, P->bwK);
@@ -498,6 +503,7 @@ void build_problem(tt_ctx* c, tt_problem* P, const tt_problem_desc* d) {
     P->n_nodes = d->n_nodes; P->n_elem = d->n_elem; P->n_p = d->n_pnodes;
     P->m = d->m; P->n_xi = d->n_xi; P->n_t = d->n_t; P->tau = d->tau; P->h = d->h;
     const int n = d->n_nodes, E = d->n_elem, np_ = d->n_pnodes;
+    P->hxy.assign(d->xy, d->xy + 2 * (size_t)n);
     P->fidx.assign(n, -1);
     P->didx.assign(n, -1);
     int nf = 0, nd = 0;

@@ -719,7 +719,7 @@ void left_svd(tt_ctx* c, int m, int n, MatView A, double* sig, double* U, double
 
 // ============================================================== truncation
 namespace {
-__global__ void k_trunc_first(const double* __restrict__ s, int p, double eps, TruncInfo* info) {
+__global__ void k_trunc_first(const double* __restrict__ s, int p, double eps, int maxr, TruncInfo* info) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double tot = 0.0;
     for (int i = p - 1; i >= 0; --i) tot += s[i] * s[i];
@@ -738,9 +738,15 @@ __global__ void k_trunc_first(const double* __restrict__ s, int p, double eps, T
         r = 0;
         for (int i = 0; i < p; ++i) r += s[i] > 0.0;
     }
-    info->r1 = r < 1 ? 1 : r;
+    if (r < 1) r = 1;
+    info->capped = 0;
+    if (maxr > 0 && r > maxr) {
+        r = maxr;
+        info->capped = 1;
+    }
+    info->r1 = r;
 }
-__global__ void k_trunc_second(const double* __restrict__ s, int p, double eps, TruncInfo* info) {
+__global__ void k_trunc_second(const double* __restrict__ s, int p, double eps, int maxr, TruncInfo* info) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const double d2 = info->delta2;
     int r = p;
@@ -755,6 +761,10 @@ __global__ void k_trunc_second(const double* __restrict__ s, int p, double eps, 
         for (int i = 0; i < p; ++i) r += s[i] > 0.0;
     }
     if (r < 1) r = 1;
+    if (maxr > 0 && r > maxr) {
+        r = maxr;
+        info->capped |= 2;
+    }
     info->r2 = r;
     double kept = 0.0;
     for (int i = r - 1; i >= 0; --i) kept += s[i] * s[i];
@@ -762,12 +772,12 @@ __global__ void k_trunc_second(const double* __restrict__ s, int p, double eps, 
 }
 }  // namespace
 
-void trunc_first(tt_ctx* c, const double* sig1, int p1, double eps, TruncInfo* dinfo) {
-    k_trunc_first<<<1, 32, 0, c->stream>>>(sig1, p1, eps, dinfo);
+void trunc_first(tt_ctx* c, const double* sig1, int p1, double eps, TruncInfo* dinfo, int maxr) {
+    k_trunc_first<<<1, 32, 0, c->stream>>>(sig1, p1, eps, maxr, dinfo);
     LAUNCH_CHECK(c);
 }
-void trunc_second(tt_ctx* c, const double* sig2, int p2, double eps, TruncInfo* dinfo) {
-    k_trunc_second<<<1, 32, 0, c->stream>>>(sig2, p2, eps, dinfo);
+void trunc_second(tt_ctx* c, const double* sig2, int p2, double eps, TruncInfo* dinfo, int maxr) {
+    k_trunc_second<<<1, 32, 0, c->stream>>>(sig2, p2, eps, maxr, dinfo);
     LAUNCH_CHECK(c);
 }
 

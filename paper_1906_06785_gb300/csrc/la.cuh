@@ -49,11 +49,12 @@ struct TruncInfo {
     double delta2;     // delta^2 = (eps ||z||)^2 / 2
     double nrm_after;  // ||T(z)||
     int r1, r2;
+    int capped;        // bit 0: r1 was cut to its cap, bit 1: r2 was
 };
-// First stage: nrm^2 = sum sig1^2, delta2, r1.
-void trunc_first(tt_ctx* c, const double* sig1, int p1, double eps, TruncInfo* dinfo);
-// Second stage: r2 and nrm_after from sig2.
-void trunc_second(tt_ctx* c, const double* sig2, int p2, double eps, TruncInfo* dinfo);
+// First stage: nrm^2 = sum sig1^2, delta2, r1 (at most maxr when maxr > 0).
+void trunc_first(tt_ctx* c, const double* sig1, int p1, double eps, TruncInfo* dinfo, int maxr = 0);
+// Second stage: r2 (at most maxr when maxr > 0) and nrm_after from sig2.
+void trunc_second(tt_ctx* c, const double* sig2, int p2, double eps, TruncInfo* dinfo, int maxr = 0);
 
 // Copy / transpose a strided matrix into a strided destination (m x n).
 void copy_mat(tt_ctx* c, int m, int n, MatView A, MatViewMut B, double alpha = 1.0);

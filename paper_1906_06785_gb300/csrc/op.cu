@@ -355,15 +355,25 @@ void op_init(tt_ctx* c, tt_op* op, tt_problem* P, const tt_t* w, int which) {
     }
 }
 
+bool op_wavg(tt_ctx* c, const tt_op* op, double* out) {
+    tt_problem* P = op->P;
+    if (!op->w) {
+        fill_zero(c, out, 2 * (size_t)P->n_nodes);
+        return false;
+    }
+    k_wavg<<<ceil_div(2 * P->n_nodes, 256), 256, 0, c->stream>>>(2 * P->n_nodes, op->kw2, P->n_t, op->cmean.p,
+                                                                  op->w->z3, out);
+    LAUNCH_CHECK(c);
+    return true;
+}
+
 void op_ensure_K(tt_ctx* c, tt_op* op) {
     if (op->kready) return;
     tt_problem* P = op->P;
     op->Kband.alloc(c, (size_t)P->n_v * (2 * P->bwK + 1));
     if (op->w) {
         DBuf<double> wavg(c, 2 * (size_t)P->n_nodes);
-        k_wavg<<<ceil_div(2 * P->n_nodes, 256), 256, 0, c->stream>>>(2 * P->n_nodes, op->kw2, P->n_t, op->cmean.p,
-                                                                      op->w->z3, wavg.p);
-        LAUNCH_CHECK(c);
+        op_wavg(c, op, wavg.p);
         assemble_K_band(c, P, wavg.p, op->Kband.p);
     } else {
         assemble_K_band(c, P, nullptr, op->Kband.p);

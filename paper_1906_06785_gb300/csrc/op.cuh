@@ -70,4 +70,7 @@ void op_init(tt_ctx* c, tt_op* op, tt_problem* P, const tt_t* w, int which);
 void op_apply(tt_ctx* c, const tt_op* op, const tt_t* u, const tt_t* p, TTPtr* ou, TTPtr* op_);
 void op_apply_mean(tt_ctx* c, const tt_op* op, const tt_t* u, TTPtr* ou);
 void op_ensure_K(tt_ctx* c, tt_op* op);
+// w_avg of eq. (11_prec) (full-node, 2 n_nodes values) into out; zeros and false
+// when the operator has no convection field
+bool op_wavg(tt_ctx* c, const tt_op* op, double* out);
 }  // namespace tt

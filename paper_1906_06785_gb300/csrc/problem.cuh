@@ -49,6 +49,7 @@ struct tt_problem {
     int n_nodes = 0, n_elem = 0, n_p = 0, n_v = 0, n_D = 0, m = 0, n_xi = 0, n_t = 0;
     double tau = 0.0, h = 0.0;
     std::vector<int> fidx, didx;            // node -> free / Dirichlet index or -1
+    std::vector<double> hxy;                // node coordinates (host copy, n_nodes x 2)
     tt::DBuf<int> eq2, eq1;                 // element connectivity
     tt::DBuf<int> node_free, node_dir;      // device copies of fidx / didx
     tt::DBuf<int> free_nodes, dir_nodes;    // free / Dirichlet index -> node
@@ -79,7 +80,9 @@ namespace tt {
 // w_k(node) = (W[(node)*ldw + col_k], W[(n_nodes + node)*ldw + col_k]) with col_k = k.
 void assemble_conv(tt_ctx* c, tt_problem* P, const double* W, int ldw, int nf, double* vals_ff,
                    double* vals_fD);
-// K = tau^-1 M + A_0 + N(w) scattered into band storage (w full-node field or null)
+// Values of K = tau^-1 M + A_0 + N(w) on the ff pattern (w full-node field or null)
+void assemble_K_vals(tt_ctx* c, tt_problem* P, const double* wfield, double* kv);
+// K = tau^-1 M + A_0 + N(w) scattered into band storage and factorised (LU)
 void assemble_K_band(tt_ctx* c, tt_problem* P, const double* wfield, double* ab);
 // Scatter ff-pattern values into band storage
 void scatter_band(tt_ctx* c, tt_problem* P, const double* vals, double* ab);

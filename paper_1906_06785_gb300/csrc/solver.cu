@@ -201,10 +201,21 @@ Vec LSCPrec::apply(const Vec& v) {
     GmresOut go;
     tt_op* o = op;
     tt_ctx* cc = c;
+    const VecOp apply_mean = [o, cc](const Vec& x) { Vec y; op_apply_mean(cc, o, x.u.get(), &y.u); return y; };
+    if (net) {
+        const tt_net* nn = net;
+        Vec u = gmres(
+            c, apply_mean, [cc, nn, o](const Vec& x) { Vec y; y.u = learned_minv(cc, nn, o, x.u.get()); return y; },
+            b, tol_inner, eps, maxit_inner, 0.0, &go);
+        inner_its += go.its;
+        if (go.converged) {
+            r.u = std::move(u.u);
+            return r;
+        }
+        ++fallbacks;
+    }
     Vec u = gmres(
-        c,
-        [o, cc](const Vec& x) { Vec y; op_apply_mean(cc, o, x.u.get(), &y.u); return y; },
-        [this](const Vec& x) { Vec y; y.u = minv(x.u.get()); return y; },
+        c, apply_mean, [this](const Vec& x) { Vec y; y.u = minv(x.u.get()); return y; },
         b, tol_inner, eps, maxit_inner, 0.0, &go);
     inner_its += go.its;
     r.u = std::move(u.u);
@@ -222,26 +233,41 @@ static VecOp full_op(tt_ctx* c, tt_op* op) {
 
 void picard(tt_ctx* c, tt_problem* P, const tt_solver_opts* o, TTPtr* uo, TTPtr* po, tt_picard_stats* st) {
     TT_REQUIRE(o, "null options");
+    TT_REQUIRE(o->precision == TT_FP64 || o->precision == TT_MIXED, "unknown precision %d", o->precision);
+    TT_REQUIRE((o->init_u == nullptr) == (o->init_p == nullptr), "init_u and init_p go together");
     memset(st, 0, sizeof(*st));
     st->fnorm = P->fnorm;
-    Vec f;
-    f.u = clone(c, P->fu);
-    f.p = clone(c, P->fp);
-    // Stokes problem (N = 0) for the initial iterate, solved to tol_gmres ||f|| (Section 5.2)
-    tt_op stokes;
-    op_init(c, &stokes, P, nullptr, TT_OP_FULL);
-    LSCPrec pre{c, &stokes, o->eps_gmres, o->tol_inner, o->maxit_inner};
-    GmresOut go;
-    Vec up;
-    {
-        PrecScope ps(c, o->mixed ? 1 : 0);
-        up = gmres(c, full_op(c, &stokes), [&pre](const Vec& v) { return pre.apply(v); }, f, o->tol_gmres,
-                   o->eps_gmres, o->maxit_gmres, P->fnorm, &go);
+    const int fast = o->precision == TT_MIXED ? 1 : 0;
+    TTPtr u{nullptr, tt_free}, p{nullptr, tt_free};
+    if (o->init_u) {
+        // resume from a given iterate (Algorithm 3.1 from step i = 0 with u^(0), p^(0))
+        TT_REQUIRE(o->init_u->n_x == 2 * P->n_v && o->init_p->n_x == P->n_p && o->init_u->n_t == P->n_t &&
+                       o->init_u->n_xi == P->n_xi && o->init_p->n_t == P->n_t && o->init_p->n_xi == P->n_xi,
+                   "initial iterate does not match the problem");
+        u = clone(c, o->init_u);
+        p = clone(c, o->init_p);
+    } else {
+        Vec f;
+        f.u = clone(c, P->fu);
+        f.p = clone(c, P->fp);
+        // Stokes problem (N = 0) for the initial iterate, solved to tol_gmres ||f|| (Section 5.2)
+        tt_op stokes;
+        op_init(c, &stokes, P, nullptr, TT_OP_FULL);
+        LSCPrec pre{c, &stokes, o->eps_gmres, o->tol_inner, o->maxit_inner, o->learned};
+        GmresOut go;
+        Vec up;
+        {
+            PrecScope ps(c, fast);
+            up = gmres(c, full_op(c, &stokes), [&pre](const Vec& v) { return pre.apply(v); }, f, o->tol_gmres,
+                       o->eps_gmres, o->maxit_gmres, P->fnorm, &go);
+        }
+        st->stokes_its = go.its;
+        st->gmres_its[0] = go.its;
+        st->inner_its[0] = pre.inner_its;
+        st->fallbacks[0] = pre.fallbacks;
+        u = std::move(up.u);
+        p = std::move(up.p);
     }
-    st->stokes_its = go.its;
-    st->gmres_its[0] = go.its;
-    st->inner_its[0] = pre.inner_its;
-    TTPtr u = std::move(up.u), p = std::move(up.p);
     TTPtr ru{nullptr, tt_free}, rp{nullptr, tt_free};
     double rn = residual(c, P, u.get(), p.get(), o->eps_gmres, &ru, &rp);
     st->res[0] = rn;
@@ -255,18 +281,20 @@ void picard(tt_ctx* c, tt_problem* P, const tt_solver_opts* o, TTPtr* uo, TTPtr*
         st->conv_ranks[i][0] = wt->r1; st->conv_ranks[i][1] = wt->r2;
         tt_op L;
         op_init(c, &L, P, wt.get(), TT_OP_FULL);
-        LSCPrec pr{c, &L, o->eps_gmres, o->tol_inner, o->maxit_inner};
+        LSCPrec pr{c, &L, o->eps_gmres, o->tol_inner, o->maxit_inner, o->learned};
         Vec r;
         r.u = std::move(ru);
         r.p = std::move(rp);
         Vec d;
+        GmresOut go;
         {
-            PrecScope ps(c, o->mixed ? 1 : 0);
+            PrecScope ps(c, fast);
             d = gmres(c, full_op(c, &L), [&pr](const Vec& v) { return pr.apply(v); }, r, o->tol_gmres,
                       o->eps_gmres, o->maxit_gmres, rn, &go);
         }
         st->gmres_its[i] = go.its;
         st->inner_its[i] = pr.inner_its;
+        st->fallbacks[i] = pr.fallbacks;
         u = round_tt(c, concat(c, {Summand{1.0, nullptr, u.get()}, Summand{1.0, nullptr, d.u.get()}}).get(), o->eps_soln);
         p = round_tt(c, concat(c, {Summand{1.0, nullptr, p.get()}, Summand{1.0, nullptr, d.p.get()}}).get(), o->eps_soln);
         rn = residual(c, P, u.get(), p.get(), o->eps_gmres, &ru, &rp);

@@ -17,18 +17,24 @@
 
 namespace tt {
 
-tt_t* tt_alloc(tt_ctx* c, int n_t, int n_xi, int n_x, int r1, int r2) {
+tt_t* tt_alloc(tt_ctx* c, int n_t, int n_xi, int n_x, int r1, int r2, int cap1, int cap2) {
     TT_REQUIRE(n_t > 0 && n_xi > 0 && n_x > 0 && r1 > 0 && r2 > 0,
                "bad train shape %d %d %d ranks %d %d", n_t, n_xi, n_x, r1, r2);
+    if (cap1 <= 0) cap1 = r1;
+    if (cap2 <= 0) cap2 = r2;
+    TT_REQUIRE(cap1 >= r1 && cap2 >= r2, "rank capacities (%d, %d) below the ranks (%d, %d)", cap1, cap2, r1, r2);
+    // cores packed with the current ranks at offsets fixed by the capacities
+    const size_t s1 = (size_t)n_t * cap1, s2 = (size_t)cap1 * n_xi * cap2, s3 = (size_t)n_x * cap2;
     tt_t* t = new tt_t;
     t->ctx = c;
     t->n_t = n_t; t->n_xi = n_xi; t->n_x = n_x; t->r1 = r1; t->r2 = r2;
-    const size_t s1 = (size_t)n_t * r1, s2 = (size_t)r1 * n_xi * r2, s3 = (size_t)n_x * r2;
-    cudaError_t e = cudaMallocAsync((void**)&t->base, (s1 + s2 + s3) * sizeof(double), c->stream);
-    if (e != cudaSuccess) {
+    t->cap1 = cap1; t->cap2 = cap2;
+    t->bytes = (s1 + s2 + s3) * sizeof(double);
+    try {
+        t->base = static_cast<double*>(ctx_malloc(c, t->bytes));
+    } catch (...) {
         delete t;
-        TT_THROW(TT_ENOMEM, "train allocation of %zu doubles failed: %s", s1 + s2 + s3,
-                 cudaGetErrorString(e));
+        throw;
     }
     t->z1 = t->base;
     t->z2 = t->base + s1;
@@ -38,7 +44,7 @@ tt_t* tt_alloc(tt_ctx* c, int n_t, int n_xi, int n_x, int r1, int r2) {
 
 void tt_free(tt_t* t) {
     if (!t) return;
-    if (t->base) cudaFreeAsync(t->base, t->ctx->stream);
+    if (t->base) ctx_free(t->ctx, t->base, t->bytes);
     delete t;
 }
 
@@ -48,10 +54,20 @@ TTPtr zeros(tt_ctx* c, int n_t, int n_xi, int n_x) {
     return t;
 }
 
+void copy_cores(tt_ctx* c, const tt_t* s, tt_t* t) {
+    TT_REQUIRE(t->cap1 >= s->r1 && t->cap2 >= s->r2 && t->n_t == s->n_t && t->n_xi == s->n_xi && t->n_x == s->n_x,
+               "copy_cores: destination (capacity %d, %d) cannot hold ranks (%d, %d)", t->cap1, t->cap2, s->r1, s->r2);
+    t->r1 = s->r1;
+    t->r2 = s->r2;
+    const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+    CUDA_CHECK(cudaMemcpyAsync(t->z1, s->z1, (size_t)s->n_t * s->r1 * sizeof(double), k, c->stream));
+    CUDA_CHECK(cudaMemcpyAsync(t->z2, s->z2, (size_t)s->r1 * s->n_xi * s->r2 * sizeof(double), k, c->stream));
+    CUDA_CHECK(cudaMemcpyAsync(t->z3, s->z3, (size_t)s->n_x * s->r2 * sizeof(double), k, c->stream));
+}
+
 TTPtr clone(tt_ctx* c, const tt_t* s, double scale) {
     TTPtr t = wrap(tt_alloc(c, s->n_t, s->n_xi, s->n_x, s->r1, s->r2));
-    const size_t tot = (size_t)s->n_t * s->r1 + (size_t)s->r1 * s->n_xi * s->r2 + (size_t)s->n_x * s->r2;
-    CUDA_CHECK(cudaMemcpyAsync(t->base, s->base, tot * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    copy_cores(c, s, t.get());
     if (scale != 1.0) copy_mat(c, s->n_t, s->r1, colmaj(t->z1, s->n_t), colmaj(t->z1, s->n_t), scale);
     return t;
 }
@@ -143,7 +159,7 @@ __global__ void k_sqrt_abs(int n, double* __restrict__ v) {
 // (no QR).  One-sided Jacobi on a symmetric PSD matrix returns its eigenvectors
 // with column norms equal to the eigenvalues.  Eigenvalues carry an absolute
 // error of order n eps_mach ||z||^2, far below delta^2 = eps^2 ||z||^2 / 2 here.
-static TTPtr round_gram(tt_ctx* c, const tt_t* z, double eps, RoundOut* info) {
+static TTPtr round_gram(tt_ctx* c, const tt_t* z, double eps, RoundOut* info, int cap1, int cap2) {
     PrecScope fp64(c, 0);
     const int n_t = z->n_t, n_xi = z->n_xi, n_x = z->n_x, R1 = z->r1, R2 = z->r2;
     // G3 = z3^T z3 costs 2 R2^2 (n_x + R1 n_xi) flops, X = z2_left z3^T costs 2 R1 n_xi R2 n_x
@@ -174,7 +190,7 @@ static TTPtr round_gram(tt_ctx* c, const tt_t* z, double eps, RoundOut* info) {
     k_sqrt_abs<<<ceil_div(n_t, 256), 256, 0, c->stream>>>(n_t, sig1.p);
     LAUNCH_CHECK(c);
     DBuf<TruncInfo> dinfo(c, 1);
-    trunc_first(c, sig1.p, n_t, eps, dinfo.p);
+    trunc_first(c, sig1.p, n_t, eps, dinfo.p, cap1);
     TruncInfo h;
     read_back(c, dinfo.p, &h, 1);
     check_status(c);
@@ -205,7 +221,7 @@ static TTPtr round_gram(tt_ctx* c, const tt_t* z, double eps, RoundOut* info) {
     left_svd(c, m, m, colmaj(S2.p, m), sig2.p, U2.p);
     k_sqrt_abs<<<ceil_div(m, 256), 256, 0, c->stream>>>(m, sig2.p);
     LAUNCH_CHECK(c);
-    trunc_second(c, sig2.p, m, eps, dinfo.p);
+    trunc_second(c, sig2.p, m, eps, dinfo.p, cap2);
     read_back(c, dinfo.p, &h, 1);
     check_status(c);
     const int r2 = h.r2;
@@ -219,6 +235,7 @@ static TTPtr round_gram(tt_ctx* c, const tt_t* z, double eps, RoundOut* info) {
     if (info) {
         info->nrm_before = h.nrm;
         info->nrm_after = h.nrm_after;
+        info->capped = h.capped;
     }
     static const bool log = getenv("TT_LOG_ROUND") != nullptr;
     if (log)
@@ -231,7 +248,7 @@ static TTPtr round_gram(tt_ctx* c, const tt_t* z, double eps, RoundOut* info) {
 // column space (left singular vectors, FP64) and absorb U0^T z1 into the middle
 // core: the same tensor with first rank <= n_t, so every later product and factor
 // of the truncation works on n_t instead of R1 rows of the middle core.
-TTPtr round_tt(tt_ctx* c, const tt_t* z, double eps, RoundOut* info) {
+TTPtr round_tt(tt_ctx* c, const tt_t* z, double eps, RoundOut* info, int cap1, int cap2) {
     if (z->r1 > z->n_t) {
         const int n_t = z->n_t, n_xi = z->n_xi, R1 = z->r1, R2 = z->r2;
         DBuf<double> sig(c, n_t), U0(c, (size_t)n_t * n_t);
@@ -248,11 +265,11 @@ TTPtr round_tt(tt_ctx* c, const tt_t* z, double eps, RoundOut* info) {
         view.r1 = n_t;
         view.z1 = U0.p;
         view.z2 = z2c.p;
-        return round_tt(c, &view, eps, info);
+        return round_tt(c, &view, eps, info, cap1, cap2);
     }
     // plain FP64 path: Gram route for tolerances well above sqrt(eps_mach); the mixed
     // path keeps the R-factor route, whose products it runs in FP32
-    if (eps >= kGramMinEps && c->gram_ok && !c->fast) return round_gram(c, z, eps, info);
+    if (eps >= kGramMinEps && c->gram_ok && !c->fast) return round_gram(c, z, eps, info, cap1, cap2);
     const int n_t = z->n_t, n_xi = z->n_xi, n_x = z->n_x, R1 = z->r1, R2 = z->r2;
     // 1. R3 with z3 = Q3 R3 (z3: n_x x R2 row-major, Q3 orthonormal columns).  Q3 = I
     //    with R3 = z3 is always a valid choice; a Householder R factor (k = R2 rows)
@@ -290,7 +307,7 @@ TTPtr round_tt(tt_ctx* c, const tt_t* z, double eps, RoundOut* info) {
     const double jtol = eps > 0.0 ? std::min(1e-8, std::max(1e-13, 1e-3 * eps)) : 1e-13;
     left_svd(c, n_t, k1, colmaj(A1.p, n_t), sig1.p, U1.p, jtol);
     DBuf<TruncInfo> dinfo(c, 1);
-    trunc_first(c, sig1.p, p1, eps, dinfo.p);
+    trunc_first(c, sig1.p, p1, eps, dinfo.p, cap1);
     TruncInfo h;
     read_back(c, dinfo.p, &h, 1);
     check_status(c);
@@ -315,7 +332,7 @@ TTPtr round_tt(tt_ctx* c, const tt_t* z, double eps, RoundOut* info) {
     const int p2 = std::min(m, k);
     DBuf<double> sig2(c, p2), U2(c, (size_t)m * p2);
     left_svd(c, m, k, colmaj(Y.p, m), sig2.p, U2.p, jtol);
-    trunc_second(c, sig2.p, p2, eps, dinfo.p);
+    trunc_second(c, sig2.p, p2, eps, dinfo.p, cap2);
     read_back(c, dinfo.p, &h, 1);
     check_status(c);
     const int r2 = h.r2;
@@ -331,6 +348,7 @@ TTPtr round_tt(tt_ctx* c, const tt_t* z, double eps, RoundOut* info) {
     if (info) {
         info->nrm_before = h.nrm;
         info->nrm_after = h.nrm_after;
+        info->capped = h.capped;
     }
     static const bool log = getenv("TT_LOG_ROUND") != nullptr;
     if (log)

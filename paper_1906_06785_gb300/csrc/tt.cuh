@@ -20,12 +20,18 @@ constexpr double kGramMinEps = 5e-6;
 // T_eps(z); fills the norms before / after truncation.
 struct RoundOut {
     double nrm_before = 0.0, nrm_after = 0.0;
+    int capped = 0;   // nonzero: a rank was cut to its cap (the error bound may not hold)
 };
-TTPtr round_tt(tt_ctx* c, const tt_t* z, double eps, RoundOut* info = nullptr);
+// cap1, cap2 > 0 bound the output ranks (the truncation then keeps the leading
+// singular triplets up to the cap and reports it in info->capped).
+TTPtr round_tt(tt_ctx* c, const tt_t* z, double eps, RoundOut* info = nullptr, int cap1 = 0, int cap2 = 0);
 
 // <vec a, vec b> written to the device scalar *dout.
 void dot_dev(tt_ctx* c, const tt_t* a, const tt_t* b, double* dout);
 double dot_host(tt_ctx* c, const tt_t* a, const tt_t* b);
+
+// Copy the cores of s into t (t's capacities must hold s's ranks; t takes s's ranks).
+void copy_cores(tt_ctx* c, const tt_t* s, tt_t* t);
 
 // Copy of a train (same ranks), optionally scaled by a host scalar.
 TTPtr clone(tt_ctx* c, const tt_t* t, double scale = 1.0);

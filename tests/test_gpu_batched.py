@@ -1,6 +1,8 @@
 """Batched form: independent problems solved concurrently (one context and stream
 per problem, picard_solve_batched) give the same solutions as one-by-one solves."""
 import numpy as np
+
+from ttfull import full
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -16,7 +18,7 @@ def test_batched_solves_match_sequential_solves():
     for pr in probs:
         u, p, st, code = c0.problem(pr).picard(binding.opts_from(pr.tol))
         assert code == binding.TT_OK
-        ref.append((u.full(), p.full(), st.picard_its))
+        ref.append((full(u), full(p), st.picard_its))
     streams = [torch.cuda.Stream() for _ in probs]
     ctxs = [binding.Context(stream=s.cuda_stream) for s in streams]
     handles = [c.problem(pr) for c, pr in zip(ctxs, probs)]
@@ -26,8 +28,8 @@ def test_batched_solves_match_sequential_solves():
         assert code == binding.TT_OK
         assert sec > 0.0
         assert st.picard_its == rits
-        assert np.linalg.norm(u.full() - ru) <= 1e-12 * np.linalg.norm(ru)
-        assert np.linalg.norm(p.full() - rp) <= 1e-12 * np.linalg.norm(rp)
+        assert np.linalg.norm(full(u) - ru) <= 1e-12 * np.linalg.norm(ru)
+        assert np.linalg.norm(full(p) - rp) <= 1e-12 * np.linalg.norm(rp)
 
 
 def test_batched_rejects_problems_sharing_a_context():

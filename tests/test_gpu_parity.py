@@ -14,6 +14,8 @@ import numpy as np
 import pytest
 import scipy.sparse as sp
 
+from ttfull import full
+
 import synth
 from oracle import tt as otm
 from oracle.system import Discretisation
@@ -72,7 +74,7 @@ def test_dot_and_axpby(ctx, shape):
     s = ctx.axpby(0.3, a, -1.7, b)
     ref = otm.add((0.3, oa), (-1.7, ob))
     assert s.ranks == ref.ranks
-    assert _rel(s.full(), ref.full()) < 1e-14
+    assert _rel(full(s), ref.full()) < 1e-14
 
 
 # ------------------------------------------------------------------ truncation
@@ -112,16 +114,16 @@ def test_round_matches_oracle(ctx, shape, eps):
 def test_round_zero_and_rank_one(ctx):
     z = ctx.tt(np.zeros((5, 2)), np.zeros((2, 3, 2)), np.zeros((2, 9)))
     g, nb, na = ctx.round(z, 1e-3)
-    assert nb == 0.0 and g.ranks == (1, 1) and not g.full().any()
+    assert nb == 0.0 and g.ranks == (1, 1) and not full(g).any()
     one = ctx.tt(*synth.random_tt(5, 3, 9, 1, 1, seed=9))
     g, nb, _ = ctx.round(one, 1e-12)
-    assert g.ranks == (1, 1) and _rel(g.full(), one.full()) < 1e-14
+    assert g.ranks == (1, 1) and _rel(full(g), one.full()) < 1e-14
 
 
 def test_round_keeps_everything_at_eps_zero(ctx):
     z = synth.random_tt(8, 3, 50, 4, 6, seed=11)
     g, nb, na = ctx.round(ctx.tt(*z), 0.0)
-    assert _rel(g.full(), otm.TT(*z).full()) < 1e-13
+    assert _rel(full(g), otm.TT(*z).full()) < 1e-13
     assert abs(nb - na) < 1e-13 * nb
 
 
@@ -160,11 +162,11 @@ def test_rhs_and_lifting(ctx, name, tiny, small):
     P = ctx.problem(prob)
     fu, fp = P.rhs()
     rfu, rfp = d.rhs()
-    assert _rel(fu.full(), rfu.full()) < 1e-12
-    assert _rel(fp.full(), rfp.full()) < 1e-12
+    assert _rel(full(fu), rfu.full()) < 1e-12
+    assert _rel(full(fp), rfp.full()) < 1e-12
     u, _, gu, _ = _pair(ctx, d, 21)
     w = P.full_velocity(gu)
-    assert _rel(w.full(), d.full_velocity(u).full()) < 1e-14
+    assert _rel(full(w), d.full_velocity(u).full()) < 1e-14
 
 
 @pytest.mark.parametrize("name", ["tiny", "small"])
@@ -217,7 +219,8 @@ def test_preconditioner_matches(ctx, name, tiny, small):
     w = d.full_velocity(otm.TT(*synth.random_tt(d.n_t, d.n_xi, d.n_u, 2, 2, seed=91)).scale(0.3))
     op = P.op(ctx.tt(w.z1, w.z2, w.z3))
     eps, tol_in = 1e-12, 1e-9
-    gu2, gp2, its = op.prec(gu, gp, eps, tol_in, 40)
+    gu2, gp2, its, fb = op.prec(gu, gp, eps, tol_in, 40)
+    assert fb == 0
     pre = MeanLSC(d, w, eps, tol_in, 40)
     ou, opp = pre((u, p))
     assert _tt_diff(_oracle_tt(gp2), opp) < 1e-10
@@ -239,8 +242,8 @@ def test_gmres_matches(ctx, tiny):
                            maxit=t.maxit_gmres, space=_Pair)
     assert code == binding.TT_OK
     assert st.its == ost["its"]
-    assert _rel(zu.full(), ou.full()) < 1e-8
-    assert _rel(zp.full(), opp.full()) < 1e-8
+    assert _rel(full(zu), ou.full()) < 1e-8
+    assert _rel(full(zp), opp.full()) < 1e-8
 
 
 # ------------------------------------------------------------------ end to end
@@ -259,8 +262,8 @@ def test_picard_tiny_tight(ctx):
     t.eps_gmres, t.eps_soln, t.eps_conv = 1e-12, 1e-13, 1e-12
     u, p, st, code, ou, op_, ost = _picard_pair(ctx, prob)
     assert code == 0 and st.picard_its == ost["picard_its"]
-    assert _rel(u.full(), ou.full()) < 1e-8
-    assert _rel(p.full(), op_.full()) < 1e-8
+    assert _rel(full(u), ou.full()) < 1e-8
+    assert _rel(full(p), op_.full()) < 1e-8
 
 
 def test_picard_tiny_default_tolerances(ctx):
@@ -270,8 +273,8 @@ def test_picard_tiny_default_tolerances(ctx):
     assert code == 0
     assert st.picard_its == ost["picard_its"]
     assert list(st.gmres_its[1:st.picard_its + 1]) == ost["gmres_its"]
-    assert _rel(u.full(), ou.full()) < 1e-6
-    assert _rel(p.full(), op_.full()) < 1e-6
+    assert _rel(full(u), ou.full()) < 1e-6
+    assert _rel(full(p), op_.full()) < 1e-6
     assert st.res[st.picard_its] <= prob.tol.tol_picard * st.fnorm
 
 

@@ -63,7 +63,7 @@ def test_small_picard_matches_oracle(ctx, mixed, tol):
     g = _golden("small")
     prob = synth.preset("small")
     P = ctx.problem(prob)
-    u, p, st, code = P.picard(binding.opts_from(prob.tol, mixed=mixed))
+    u, p, st, code = P.picard(binding.opts_from(prob.tol, precision=mixed))
     assert code == binding.TT_OK
     assert st.res[st.picard_its] <= prob.tol.tol_picard * st.fnorm
     assert _sample_err(u, g["u"]) < tol
