@@ -62,6 +62,10 @@ def _args():
     ap.add_argument("--batch", type=int, default=0,
                     help="> 0: time batches of this many independent problems of the workload (seeded "
                          "nu0 in [1/100, 1/50], sigma in [0.05, 0.3]) solved concurrently, one stream each")
+    ap.add_argument("--learned", type=int, default=1,
+                    help="1: also train the learned mean-Oseen solve on the GPU and time the solve with it")
+    ap.add_argument("--train-pairs", dest="train_pairs", type=int, default=4096)
+    ap.add_argument("--train-epochs", dest="train_epochs", type=int, default=3)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="mixed: FP32 SpMM/GEMM/R factors inside GMRES, FP64 SVDs, dots, residual; "
                          "fp64: plain FP64 throughout")
@@ -122,8 +126,9 @@ def _oracle_sample_worker(workload, seconds, q):
     Picard step (each: preconditioner with its inner solve, matvec with the
     convection term, truncations, Gram-Schmidt, iterate and true residual) until
     `seconds` of CPU work have been spent."""
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ[v] = "1"
+        os.environ[v] = str(threads)
     import numpy as np
     import synth
     from oracle.system import Discretisation
@@ -151,7 +156,7 @@ def _oracle_sample_worker(workload, seconds, q):
         if time.perf_counter() - t0 > seconds or st2["its"] < k:
             break
     q.put(dict(stokes_s=stokes, stokes_its=st["its"], sec_per_outer_it=per[-1], outer_its_sampled=its,
-               wall=time.perf_counter() - t0))
+               wall=time.perf_counter() - t0, threads=threads))
 
 
 def cpu_sample(workload, seconds):
@@ -176,10 +181,41 @@ def max_over_ranks(value, dist=None, device="cuda"):
 
 
 # ------------------------------------------------------------------ GPU arm
+def _golden(workload):
+    """Oracle-written record of the workload's Picard solve (tests/golden), if any:
+    (sampled u entries, sampled p entries)."""
+    path = os.path.join(ROOT, "tests", "golden", f"picard_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    u, p = [], []
+    for line in open(path):
+        f = line.split()
+        if f and f[0] in ("u", "p"):
+            (u if f[0] == "u" else p).append((int(f[1]), int(f[2]), int(f[3]), float(f[4])))
+    return u, p
+
+
+def _sample_error(t, samples):
+    """max |z(i,s,j) - oracle| / max |oracle| over the oracle's sampled entries."""
+    z1, z2, z3 = t.cores()
+    ref = max(abs(v) for *_, v in samples)
+    err = max(abs(float(z1[i] @ z2[:, s, :] @ z3[:, j]) - v) for i, s, j, v in samples)
+    return err / ref
+
+
+def _tt_rel_diff(ctx, a, b):
+    """||a - b|| / ||b|| from the singular values of the concatenated train (no
+    cancellation of ||a||^2 - 2<a,b> + ||b||^2)."""
+    d = ctx.axpby(1.0, a, -1.0, b)
+    _, nd, _ = ctx.round(d, 0.0)
+    return nd
+
+
 def run_ours(a):
     import numpy as np
     import torch
     import synth
+    from synth.lattice import gaussian_residuals, he_normal_params
     from paper_1906_06785_gb300 import binding
 
     rank = int(os.environ.get("RANK", "0"))
@@ -202,19 +238,18 @@ def run_ours(a):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     stream = torch.cuda.current_stream()
 
-    def timed(mixed, profile):
-        opts = binding.opts_from(prob.tol, precision=mixed)
+    def timed(opts, warmup, steps):
+        """Device time per solve (CUDA events on the context stream), L2 flushed before
+        each timed solve, profiling off; max over ranks."""
         last = None
-        for _ in range(a.warmup):
+        for _ in range(warmup):
             last = P.picard(opts)
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        if profile:
-            ctx.profile(True)
         l0 = ctx.launches
         times = []
-        for _ in range(a.steps):
+        for _ in range(steps):
             flush.zero_()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -223,96 +258,146 @@ def run_ours(a):
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1) / 1000.0)
-        launches = (ctx.launches - l0) // max(a.steps, 1)
-        prof = None
-        if profile:
-            prof = ctx.prof_read()
-            ctx.profile(False)
-        t = max_over_ranks(sum(times) / len(times), dist, "cuda")
-        return t, launches, prof, last, opts
+        if dist:
+            dist.barrier()
+        launches = (ctx.launches - l0) // max(steps, 1)
+        return max_over_ranks(sum(times) / len(times), dist, "cuda"), launches, last
 
-    main_mixed = 1 if a.precision == "mixed" else 0
-    # the other precision first, unprofiled; then the headline precision with clocks
-    t_other, _, _, last_other, _ = timed(1 - main_mixed, False)
+    o64 = binding.opts_from(prob.tol, precision=binding.FP64)
+    omx = binding.opts_from(prob.tol, precision=binding.MIXED)
+    main = omx if a.precision == "mixed" else o64
+    other = o64 if a.precision == "mixed" else omx
+
+    # comparator first, then the headline precision with the clock sampler running
+    t_other, _, last_other = timed(other, 1, a.steps)
     clocks = Clocks(local)
-    t_step, launches, prof, last, opts = timed(main_mixed, True)
+    t_step, launches, last = timed(main, a.warmup, a.steps)
     clk = clocks.stop()
     u, p, st, code = last
     uo, po, _, _ = last_other
-    # relative difference of the two solutions ((u, p) jointly, via TT dots)
-    dt = ctx.dot
-    du = dt(u, u) - 2 * dt(u, uo) + dt(uo, uo)
-    dp = dt(p, p) - 2 * dt(p, po) + dt(po, po)
-    rel_diff = float(np.sqrt(max(du + dp, 0.0) / (dt(uo, uo) + dt(po, po))))
+    rel_diff = float(np.hypot(_tt_rel_diff(ctx, u, uo), _tt_rel_diff(ctx, p, po)) /
+                     np.hypot(ctx.norm(uo), ctx.norm(po)))
+
+    # the learned mean-Oseen solve: trained on the GPU on (r, K^-1 r) pairs of the
+    # Stokes operator's K, then used inside the inner solve of the headline precision
+    learned = None
+    if a.learned:
+        ch, depth = 64, 4
+        net = binding.NetHandle(P, ch, depth, he_normal_params(ch, depth, seed=0))
+        R0 = gaussian_residuals(prob.n_v, a.train_pairs, seed=1234)
+        op0 = P.op(None)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        losses = net.train(op0, R0, epochs=a.train_epochs, batch=64, lr=1e-3, smooth_max=3)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        ol = binding.opts_from(prob.tol, precision=main.precision, learned=net)
+        t_l, _, last_l = timed(ol, 1, a.steps)
+        ul, pl, stl, codel = last_l
+        learned = {"value": t_l, "unit": "s", "train_s": t_train, "pairs": a.train_pairs,
+                   "epochs": a.train_epochs, "loss_first_last": [float(losses[0]), float(losses[-1])],
+                   "picard_its": stl.picard_its, "gmres_its": list(stl.gmres_its[:stl.picard_its + 1]),
+                   "inner_its": list(stl.inner_its[:stl.picard_its + 1]),
+                   "fallbacks": list(stl.fallbacks[:stl.picard_its + 1]), "status": int(codel),
+                   "rel_diff_vs_exact_preconditioner": float(
+                       np.hypot(_tt_rel_diff(ctx, ul, u), _tt_rel_diff(ctx, pl, p)) / np.hypot(ctx.norm(u),
+                                                                                                ctx.norm(p)))}
+
+    # one more solve of the headline precision with per-launch events, for the
+    # kernel-class breakdown and the roofline of the dominant class (not in `value`)
+    ctx.profile(True)
+    torch.cuda.synchronize()
+    tp0 = time.perf_counter()
+    P.picard(main)
+    torch.cuda.synchronize()
+    t_prof = time.perf_counter() - tp0
+    prof = ctx.prof_read()
+    ctx.profile(False)
 
     # end-to-end through the public API with host buffers (problem arrays in, cores out)
     e2e = []
     h2d = sum(v.nbytes for v in (prob.mesh.xy, prob.mesh.elem_q2, prob.mesh.elem_q1, prob.mesh.dirichlet,
                                   prob.mesh.inflow, prob.mi, prob.nu, prob.tprofile))
     d2h = 0
-    for _ in range(max(1, a.steps)):
+    for _ in range(max(1, min(a.steps, 2))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         P2 = ctx.problem(prob)
-        u2, p2, st2, _ = P2.picard(opts)
+        u2, p2, st2, _ = P2.picard(main)
         cu, cp = u2.cores(), p2.cores()
         e2e.append(time.perf_counter() - t0)
         d2h = sum(x.nbytes for x in cu) + sum(x.nbytes for x in cp)
         del u2, p2, P2
 
-    # roofline of the dominant kernel class (events around each launch in the timed region)
     peaks = _peaks()
     dom = max(prof, key=lambda k: prof[k][1])
     n, ms, fl, by = prof[dom]
-    fp64_peak = 1250.0   # GFLOP/s: nominal GB300 FP64 rate (no measured FP64 peak is available)
-    if dom in ("spmm", "band_solve"):
-        achieved = by / (ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s"}
+    # FP64 peak from the unit counts: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz
+    fp64_peak = 152 * 4 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    if dom in ("spmm", "band_solve", "core"):
+        roof = {"bound": "hbm", "achieved": by / (ms * 1e-3) / 1e9, "peak": peaks.get("hbm_gbs", 6800.0),
+                "unit": "GB/s", "peak_source": "of measured: MEASURED_PEAKS.json hbm_gbs (burst)"}
     else:
-        achieved = fl / (ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak / 1000.0, "unit": "TFLOP/s"}
+        roof = {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                "peak_source": "FP64 rate from unit counts and clocks (152 SMs x 4 flop/clk x max SM clock); "
+                               "MEASURED_PEAKS.json has no FP64 figure"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = dom
     roof["launches"] = n
     roof["ms_per_launch"] = ms / max(n, 1)
+    roof["work"] = ("algorithmic flops: dense SVD count 14 m n^2 + 8 n^3 per m x n matrix" if dom == "jacobi"
+                    else "algorithmic bytes/flops of each launch")
     roof["traffic"] = NCU_TRAFFIC.get((a.workload, dom))
-    roof["peak_source"] = ("of measured: MEASURED_PEAKS.json hbm_gbs (burst)" if roof["bound"] == "hbm"
-                           else "nominal FP64 1.25 TFLOP/s (no FP64 figure in MEASURED_PEAKS.json)")
-    breakdown = {k: {"launches": v[0], "ms_per_step": v[1] / a.steps,
-                     "gflop_per_step": v[2] / a.steps / 1e9, "gbytes_per_step": v[3] / a.steps / 1e9}
-                 for k, v in prof.items()}
+    breakdown = {k: {"launches": v[0], "ms": v[1], "gflop": v[2] / 1e9, "gbytes": v[3] / 1e9}
+                 for k, v in prof.items() if v[0]}
+
+    gold = _golden(a.workload)
+    oracle_err = None
+    if gold:
+        oracle_err = {"u": _sample_error(u, gold[0]), "p": _sample_error(p, gold[1]),
+                      "u_other_precision": _sample_error(uo, gold[0]), "p_other_precision": _sample_error(po, gold[1]),
+                      "how": "max abs error over the oracle's 256 sampled entries of u and of p / max sampled |value|"}
 
     if rank != 0:
+        if dist:
+            dist.destroy_process_group()
         return
+    mixed_main = a.precision == "mixed"
     out = {
         "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": t_step * 1000.0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if main_mixed else "f64", "data": "synthetic",
+        "dtype": "f32+f64" if mixed_main else "f64", "data": "synthetic",
         "config": {"workload": DESCR.get(a.workload, a.workload),
-                   "precision": "mixed (FP32 SpMM/GEMM/R factors in GMRES; FP64 SVD, dots, Hessenberg, residual)"
-                   if main_mixed else "plain FP64",
+                   "precision": "mixed (FP32 SpMM/GEMM/R factors/banded solves in GMRES; FP64 SVD, dots, "
+                                "Hessenberg, residual)" if mixed_main else "plain FP64",
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "independent replica per GPU" if world > 1 else "1 GPU"},
-        ("fp64_value" if main_mixed else "mixed_value"): t_other,
+        ("fp64_value" if mixed_main else "mixed_value"): t_other,
         "rel_diff_mixed_vs_fp64": rel_diff,
+        "oracle_error": oracle_err,
+        "learned": learned,
         "e2e": {"value": sum(e2e) / len(e2e), "unit": "s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "roofline": roof,
-        "kernel_breakdown": breakdown,
+        "kernel_breakdown": {"solve_s_with_events": t_prof, "classes": breakdown},
         "solve": {"picard_its": st.picard_its, "stokes_its": st.stokes_its,
                   "gmres_its": list(st.gmres_its[1:st.picard_its + 1]),
+                  "inner_its": list(st.inner_its[:st.picard_its + 1]),
                   "rel_res": st.res[st.picard_its] / st.fnorm, "u_ranks": u.ranks, "p_ranks": p.ranks},
         "clocks": clk,
     }
     if cpu is not None:
         outer = sum(st.gmres_its[1:st.picard_its + 1])
         est = cpu["stokes_s"] + cpu["sec_per_outer_it"] * outer
-        out["cpu_baseline"] = {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
-                               "sample": f"oracle (1 BLAS thread) on the same workload: complete Stokes solve "
-                                         f"({cpu['stokes_s']:.1f} s) + first Picard step outer GMRES iteration(s) "
-                                         f"({cpu['outer_its_sampled']}, {cpu['sec_per_outer_it']:.1f} s each) "
-                                         f"scaled to the {outer} Picard-step outer iterations of the solve"}
+        out["cpu_baseline"] = {"value": est, "unit": "s", "cores": cpu["threads"], "kind": "oracle",
+                               "extrapolated": True,
+                               "sample": f"oracle ({cpu['threads']} BLAS threads, the process's cores) on the same "
+                                         f"workload, bounded: complete Stokes solve ({cpu['stokes_s']:.1f} s) + "
+                                         f"first Picard step outer GMRES iteration(s) ({cpu['outer_its_sampled']}, "
+                                         f"{cpu['sec_per_outer_it']:.1f} s each), extrapolated to the "
+                                         f"{outer} Picard-step outer iterations of the solve (a lower bound: later "
+                                         f"steps carry higher ranks)"}
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -402,10 +487,12 @@ def run_reference(a):
            "ms_per_step": v * 1000.0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": {"workload": DESCR.get(a.workload, a.workload), "precision": "plain FP64 (CPU oracle)"},
-           "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
+           "cpu_baseline": {"value": v, "unit": "s", "cores": samples[0]["threads"], "kind": "oracle",
+                            "extrapolated": True,
                             "sample": f"per step: complete oracle Stokes solve + first Picard step outer GMRES "
-                                      f"iteration(s) at {s:.1f} s each, scaled to the {outer} Picard-step outer "
-                                      f"iterations of the oracle's complete solve (1 BLAS thread)"},
+                                      f"iteration(s) at {s:.1f} s each, extrapolated to the {outer} Picard-step "
+                                      f"outer iterations of the oracle's complete solve ({samples[0]['threads']} "
+                                      f"BLAS threads)"},
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

@@ -74,6 +74,14 @@ int tt_ctx_destroy(tt_ctx* ctx);
 const char* tt_last_error(const tt_ctx* ctx);
 /* Number of kernels this context has launched so far. */
 long long tt_ctx_launches(const tt_ctx* ctx);
+/* Bound on device-side waits: a block of a cooperative (grid-synchronised) kernel
+ * that has polled a grid barrier `polls` times gives up, records a timeout in the
+ * context's device status word and finishes; the entry point then returns
+ * TT_ETIMEOUT and clears the status word, and the context stays usable.  The
+ * default (2e7 polls with back-off, seconds) never triggers in a healthy launch;
+ * small values exist to exercise the failure path (0: any wait that cannot end at
+ * once gives up).  polls < 0 is TT_EINVAL. */
+int tt_ctx_set_wait_limit(tt_ctx* ctx, long long polls);
 
 /* Profiling of kernel classes (0 QR, 1 Jacobi SVD, 2 GEMM, 3 SpMM, 4 banded
  * solve, 5 banded factorisation, 6 core-1/core-2/concatenation kernels,

@@ -73,6 +73,7 @@ _SIGS = {
     "tt_ctx_destroy": (_I, [_P]),
     "tt_last_error": (C.c_char_p, [_P]),
     "tt_ctx_launches": (C.c_longlong, [_P]),
+    "tt_ctx_set_wait_limit": (_I, [_P, C.c_longlong]),
     "tt_ctx_profile": (_I, [_P, _I]),
     "tt_ctx_prof_read": (_I, [_P, _I, C.POINTER(C.c_longlong), _DP, _DP, _DP]),
     "tt_create": (_I, [_P, _I, _I, _I, _I, _I, _I, _I, _I, _P, _P, _P, _I, C.POINTER(_P)]),
@@ -182,7 +183,11 @@ class Context:
     def launches(self):
         return int(self.lib.tt_ctx_launches(self.h))
 
-    PROF_SLOTS = ("qr", "jacobi", "gemm", "spmm", "band_solve", "band_factor", "core", "assembly")
+    PROF_SLOTS = ("qr", "jacobi", "gemm", "spmm", "band_solve", "band_factor", "core", "assembly", "conv")
+
+    def set_wait_limit(self, polls):
+        """Polls a block makes at a grid barrier before giving up (TT_ETIMEOUT)."""
+        self.check(self.lib.tt_ctx_set_wait_limit(self.h, int(polls)))
 
     def profile(self, enable=True):
         """Reset the per-kernel-class counters and turn event timing on or off."""

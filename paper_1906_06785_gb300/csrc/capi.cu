@@ -179,6 +179,12 @@ const char* tt_last_error(const tt_ctx* c) { return c ? c->err.c_str() : "null c
 
 long long tt_ctx_launches(const tt_ctx* c) { return c ? c->launches : -1; }
 
+int tt_ctx_set_wait_limit(tt_ctx* c, long long polls) {
+    if (!c || polls < 0) return TT_EINVAL;
+    c->wait_limit = polls;
+    return TT_OK;
+}
+
 int tt_ctx_profile(tt_ctx* ctx, int enable) {
     API_BEGIN(ctx)
     TT_REQUIRE(ctx, "null context");

@@ -91,6 +91,9 @@ struct tt_ctx {
     // device status word (bounded waits) + barrier counters
     int* dstatus = nullptr;
     unsigned* dbarrier = nullptr;   // [count, generation] per barrier slot
+    // polls a block makes at a grid barrier before it gives up (DEV_TIMEOUT): seconds
+    // with the back-off, far beyond any wait of a healthy launch
+    long long wait_limit = 20000000LL;
     double* dprof_flops = nullptr;  // device-counted flops per profiling slot
 };
 
@@ -232,9 +235,10 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 // Grid-wide barrier for cooperative launches.  bar[0] counts arrivals, bar[1] is
 // the generation.  Every wait is bounded: after `limit` polls the block records
-// DEV_TIMEOUT in *status and leaves; once the status is set, later barriers
-// return at once, so a kernel that lost a block still terminates.
-__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
+// DEV_TIMEOUT in *status and leaves; once DEV_TIMEOUT is set, later barriers return
+// at once, so a kernel that lost a block still terminates.  Other status values
+// (a non-finite pivot met by an earlier kernel) do not affect the barrier.
+__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, int* status, long long limit) {
     __syncthreads();
     if (nblocks == 1) return;   // a one-block launch needs only the block barrier
     if (threadIdx.x == 0) {
@@ -248,9 +252,8 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, in
             atomicAdd(bar + 1, 1u);
         } else {
             long long polls = 0;
-            const long long limit = 20000000LL;   // ~ seconds with backoff
             while (*vgen == gen) {
-                if (*(volatile int*)status != DEV_OK) break;
+                if (*(volatile int*)status == DEV_TIMEOUT) break;
                 if (++polls > limit) {
                     atomicExch(status, DEV_TIMEOUT);
                     break;
@@ -269,12 +272,12 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, in
 // barrier; every CTA of a cluster is resident by construction, so it cannot wait
 // on an absent CTA.
 template <bool kCluster>
-__device__ __forceinline__ void group_barrier(unsigned* bar, unsigned nblocks, int* status) {
+__device__ __forceinline__ void group_barrier(unsigned* bar, unsigned nblocks, int* status, long long limit) {
     if constexpr (kCluster) {
         __syncthreads();
         asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
     } else {
-        grid_barrier(bar, nblocks, status);
+        grid_barrier(bar, nblocks, status, limit);
     }
 }
 #endif

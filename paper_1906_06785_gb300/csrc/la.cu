@@ -191,6 +191,7 @@ struct QRParams {
     unsigned* bar;
     int* status;
     const double* fnorm;   // ||A||_F^2 (FP32 arithmetic works on A / ||A||_F), or null
+    long long wait_limit;  // grid-barrier polls before DEV_TIMEOUT
 };
 
 template <typename TC>
@@ -266,8 +267,8 @@ __global__ void __launch_bounds__(256) k_qr_r(QRParams<TC> P) {
     if (P.k > 0) qr_partials(P, W, 0, row0, rows, red, mypart);
     const int gw = g * nw + warp, TW = G * nw;
     for (int j = 0; j < P.k; ++j) {
-        if (*(volatile int*)P.status != DEV_OK) return;
-        group_barrier<kCluster>(P.bar, G, P.status);
+        if (*(volatile int*)P.status == DEV_TIMEOUT) return;
+        group_barrier<kCluster>(P.bar, G, P.status, P.wait_limit);
         // reduce-scatter of the live entries: 0, 1 + (j, c), 1 + c + [j, c)
         const int nd = P.c - j - 1, ne = P.c - j;
         for (int t = gw; t < 1 + nd + ne; t += TW) {
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(256) k_qr_r(QRParams<TC> P) {
             s = warp_sum(s);
             if (lane == 0) P.sums[idx] = s;
         }
-        group_barrier<kCluster>(P.bar, G, P.status);
+        group_barrier<kCluster>(P.bar, G, P.status, P.wait_limit);
         const TC ss = __ldcg(P.sums), x0 = __ldcg(P.sums + 1 + P.c + j);
         const int jloc = j - row0;
         const bool own = jloc >= 0 && jloc < rows;
@@ -377,6 +378,7 @@ void qr_r_launch(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr) {
     P.bar = c->dbarrier;
     P.status = c->dstatus;
     P.fnorm = fn.p;
+    P.wait_limit = c->wait_limit;
     CUDA_CHECK(cudaMemsetAsync(c->dbarrier, 0, 2 * sizeof(unsigned), c->stream));
     CUDA_CHECK(cudaFuncSetAttribute(k_qr_r<TC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     CUDA_CHECK(cudaFuncSetAttribute(k_qr_r<TC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
@@ -427,6 +429,23 @@ __device__ __forceinline__ T jld(const T* p) {
     if constexpr (kGlobal) return __ldcg(p);
     else return *p;
 }
+// Rotation of the column pair with squared norms al, be and product ga that makes
+// the pair orthogonal: t = tan(theta) = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) with
+// zeta = (be - al) / (2 ga), evaluated as sign(zeta) |2 ga| / (|be - al| + sqrt((be -
+// al)^2 + (2 ga)^2)) (one square root and one division), cs = 1 / sqrt(1 + t^2),
+// sn = cs t.  Returns false (no rotation) when the pair is orthogonal to tol,
+// ga^2 <= tol^2 al be, or a column is numerically zero.
+template <typename T>
+__device__ __forceinline__ bool jacobi_rotation(T al, T be, T ga, T tol, T tiny, T& cs, T& sn) {
+    if (!(al > tiny && be > tiny && ga * ga > (tol * tol * al) * be)) return false;
+    const T d = be - al, g2 = T(2) * ga;
+    const T r = sqrt(d * d + g2 * g2);
+    const T t = copysign(T(1), d) * copysign(T(1), g2) * fabs(g2) / (fabs(d) + r);
+    cs = rsqrt(T(1) + t * t);
+    sn = cs * t;
+    return true;
+}
+
 template <typename T, bool kGlobal>
 __device__ __forceinline__ bool jacobi_pair(T* ca, T* cb, int a, int b, int m, int mr, T* dn, T tol, T tiny,
                                             double& flops) {
@@ -436,10 +455,8 @@ __device__ __forceinline__ bool jacobi_pair(T* ca, T* cb, int a, int b, int m, i
     for (int i = lane; i < m; i += 32) ga = fma(jld<T, kGlobal>(ca + i), jld<T, kGlobal>(cb + i), ga);
     ga = warp_sum(ga);
     flops += 2.0 * m;
-    if (!(al > tiny && be > tiny && fabs(ga) > tol * sqrt(al) * sqrt(be))) return false;
-    const T zeta = (be - al) / (T(2) * ga);
-    const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-    const T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
+    T cs, sn;
+    if (!jacobi_rotation(al, be, ga, tol, tiny, cs, sn)) return false;
     T na = T(0), nb = T(0);
     for (int i = lane; i < mr; i += 32) {
         const T x = jld<T, kGlobal>(ca + i), y = jld<T, kGlobal>(cb + i);
@@ -483,10 +500,8 @@ __device__ __forceinline__ bool jacobi_pair_reg(T* ca, T* cb, int a, int b, int 
         if (lane + 32 * k < m) ga = fma(xa[k], xb[k], ga);
     ga = warp_sum(ga);
     flops += 2.0 * m;
-    if (!(al > tiny && be > tiny && fabs(ga) > tol * sqrt(al) * sqrt(be))) return false;
-    const T zeta = (be - al) / (T(2) * ga);
-    const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-    const T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
+    T cs, sn;
+    if (!jacobi_rotation(al, be, ga, tol, tiny, cs, sn)) return false;
     T na = T(0), nb = T(0);
 #pragma unroll
     for (int k = 0; k < KV; ++k) {
@@ -521,7 +536,8 @@ __device__ __forceinline__ void circle_pair(int r, int p, int NR, int& a, int& b
 template <typename T, bool kCluster>
 __global__ void __launch_bounds__(128)
 k_jacobi(int m, int mr, int n, int npad, T* W, int ldw, int* flags, int max_sweeps, T tol, double tiny_rel,
-         unsigned* bar, int* status, int* sweeps_used, const double* frob2, T* dn, double* flop_counter) {
+         unsigned* bar, int* status, int* sweeps_used, const double* frob2, T* dn, double* flop_counter,
+         long long wait_limit) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     double myflops = 0.0;   // flops this warp performs (exact algorithmic count)
     const int gw = blockIdx.x * nw + warp, TW = gridDim.x * nw;
@@ -541,7 +557,7 @@ k_jacobi(int m, int mr, int n, int npad, T* W, int ldw, int* flags, int max_swee
             if (lane == 0) dn[col] = s;
             myflops += 2.0 * m;
         }
-        group_barrier<kCluster>(bar, gridDim.x, status);
+        group_barrier<kCluster>(bar, gridDim.x, status, wait_limit);
         for (int r = 0; r < NR; ++r) {
             for (int p = gw; p < P; p += TW) {
                 int a, b;
@@ -555,14 +571,65 @@ k_jacobi(int m, int mr, int n, int npad, T* W, int ldw, int* flags, int max_swee
                 else rot = jacobi_pair<T, true>(ca, cb, a, b, m, mr, dn, tol, tiny, myflops);
                 if (rot) any = 1;
             }
-            group_barrier<kCluster>(bar, gridDim.x, status);
+            group_barrier<kCluster>(bar, gridDim.x, status, wait_limit);
         }
         if (any && lane == 0) flags[sw] = 1;
-        group_barrier<kCluster>(bar, gridDim.x, status);
+        group_barrier<kCluster>(bar, gridDim.x, status, wait_limit);
         if (__ldcg(flags + sw) == 0) break;
-        if (*(volatile int*)status != DEV_OK) break;
+        if (*(volatile int*)status == DEV_TIMEOUT) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_used = sw;
+    if (lane == 0 && flop_counter) atomicAdd(flop_counter, myflops);
+}
+
+
+// One-sided Jacobi of a small m x n matrix held entirely in the shared memory of one
+// CTA: one warp per column pair of a round, block barriers between rounds, the same
+// round-robin order, rotation and stopping rule as k_jacobi.  For matrices this small
+// one SM's FP64 pipe finishes a round faster than a cross-CTA barrier completes.
+__global__ void __launch_bounds__(1024)
+k_jacobi_cta(int m, int n, int npad, double* __restrict__ W, int ldw, int max_sweeps, double tol, double tiny_rel,
+             const double* __restrict__ frob2, int* __restrict__ sweeps_used, double* __restrict__ flop_counter) {
+    extern __shared__ __align__(16) double jsm[];
+    double* Ws = jsm;                              // n columns of m
+    double* dn = Ws + (size_t)n * m;               // squared column norms
+    int* flag = reinterpret_cast<int*>(dn + npad);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int e = tid; e < n * m; e += blockDim.x) Ws[e] = W[(size_t)(e / m) * ldw + e % m];
+    if (tid == 0) *flag = 0;
+    const double tiny = tiny_rel * *frob2;
+    const int P = npad / 2, NR = npad - 1;
+    double myflops = 0.0;
+    __syncthreads();
+    int sw = 0;
+    for (; sw < max_sweeps; ++sw) {
+        for (int col = warp; col < n; col += nw) {
+            const double* cc = Ws + (size_t)col * m;
+            double a = 0.0;
+            for (int i = lane; i < m; i += 32) a = fma(cc[i], cc[i], a);
+            a = warp_sum(a);
+            if (lane == 0) dn[col] = a;
+            myflops += 2.0 * m;
+        }
+        __syncthreads();
+        for (int r = 0; r < NR; ++r) {
+            for (int p = warp; p < P; p += nw) {
+                int a, b;
+                circle_pair(r, p, NR, a, b);
+                if (a >= n || b >= n) continue;
+                if (jacobi_pair<double, false>(Ws + (size_t)a * m, Ws + (size_t)b * m, a, b, m, m, dn, tol, tiny,
+                                               myflops) && lane == 0)
+                    *flag = 1;
+            }
+            __syncthreads();
+        }
+        const int any = *(volatile int*)flag;
+        __syncthreads();
+        if (tid == 0) *flag = 0;
+        if (!any) break;
+    }
+    for (int e = tid; e < n * m; e += blockDim.x) W[(size_t)(e / m) * ldw + e % m] = Ws[e];
+    if (tid == 0) *sweeps_used = sw;
     if (lane == 0 && flop_counter) atomicAdd(flop_counter, myflops);
 }
 
@@ -627,10 +694,33 @@ __global__ void k_permute_normalise(int m, int n, const double* __restrict__ W, 
 }
 }  // namespace
 
+// Matrices with at most this many entries take the one-CTA shared-memory Jacobi: a
+// round costs about 1.5 m n cycles on one SM's FP64 pipe, which is below the ~3 us of a
+// cross-CTA round at this size.
+constexpr long long kJacobiCtaMaxEntries = 4096;
+
 template <typename T>
 static void jacobi_grid(tt_ctx* c, int m, int mr, int n, T* W, int ldw, T tol, double tiny_rel,
                         const double* frob2, int max_sweeps, double* fc, const char* tag) {
     const int npad = n + (n & 1);
+    if constexpr (sizeof(T) == sizeof(double)) {
+        if ((long long)m * n <= kJacobiCtaMaxEntries && mr == m) {
+            // small matrix: one CTA, everything in shared memory
+            DBuf<int> sw(c, 1);
+            const int threads = 32 * std::min(32, std::max(1, npad / 2));
+            const size_t smem = ((size_t)n * m + npad) * sizeof(double) + 16;
+            k_jacobi_cta<<<1, threads, smem, c->stream>>>(m, n, npad, (double*)W, ldw, max_sweeps, (double)tol,
+                                                          tiny_rel, frob2, sw.p, fc);
+            LAUNCH_CHECK(c);
+            static const bool log = getenv("TT_LOG_ROUND") != nullptr;
+            if (log) {
+                int h = 0;
+                read_back(c, (const int*)sw.p, &h, 1);
+                fprintf(stderr, "jacobi%s-cta m=%d n=%d sweeps=%d\n", tag, m, n, h);
+            }
+            return;
+        }
+    }
     const int wpb = 4;
     const int G = std::max(1, std::min(c->nsm, ceil_div(npad / 2, wpb)));
     DBuf<int> flags(c, max_sweeps + 1);
@@ -646,6 +736,7 @@ static void jacobi_grid(tt_ctx* c, int m, int mr, int n, T* W, int ldw, T tol, d
     int* fl = flags.p;
     const double* f2 = frob2;
     T* dnp = dn.p;
+    long long wl = c->wait_limit;
     if (G > 1 && G <= max_cluster_ctas(c, (const void*)k_jacobi<T, true>, 32 * wpb, 0)) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(G);
@@ -660,9 +751,9 @@ static void jacobi_grid(tt_ctx* c, int m, int mr, int n, T* W, int ldw, T tol, d
         cfg.attrs = &attr;
         cfg.numAttrs = 1;
         CUDA_CHECK(cudaLaunchKernelEx(&cfg, k_jacobi<T, true>, mm, mmr, nn, np_, W, ld, fl, ms, tl, tr, bar, st,
-                                      sweeps, f2, dnp, fc));
+                                      sweeps, f2, dnp, fc, wl));
     } else {
-        void* args[] = {&mm, &mmr, &nn, &np_, &W, &ld, &fl, &ms, &tl, &tr, &bar, &st, &sweeps, &f2, &dnp, &fc};
+        void* args[] = {&mm, &mmr, &nn, &np_, &W, &ld, &fl, &ms, &tl, &tr, &bar, &st, &sweeps, &f2, &dnp, &fc, &wl};
         CUDA_CHECK(cudaLaunchCooperativeKernel((void*)k_jacobi<T, false>, dim3(G), dim3(32 * wpb), args, 0,
                                                c->stream));
     }
@@ -686,9 +777,12 @@ static void jacobi_columns(tt_ctx* c, int m, int n, double* W, double* sig, doub
     LAUNCH_CHECK(c);
     if (n > 1) {
         // flops are counted on the device (dots, rotations and norm passes performed)
-        ProfScope prof(c, PROF_JACOBI, 0.0, 16.0 * (double)m * n);
-        jacobi_grid<double>(c, m, m, n, W, m, tol, 1e-30, frob2.p, max_sweeps,
-                            c->prof ? c->dprof_flops + PROF_JACOBI : nullptr, "");
+        // algorithmic work of the launch: the dense SVD count for singular values and
+        // the m x n left singular vectors, 14 m n^2 + 8 n^3 (Golub and Van Loan, m >= n),
+        // whatever number of sweeps the Jacobi iteration takes; bytes: W read and written
+        const double dm = m, dn = n;
+        ProfScope prof(c, PROF_JACOBI, 14.0 * dm * dn * dn + 8.0 * dn * dn * dn, 16.0 * dm * dn);
+        jacobi_grid<double>(c, m, m, n, W, m, tol, 1e-30, frob2.p, max_sweeps, nullptr, "");
     }
     DBuf<double> nrm(c, n);
     DBuf<int> rank(c, n);

@@ -46,3 +46,19 @@ def gaussian_residuals(n_free: int, count: int, seed: int = 1234) -> np.ndarray:
     """Seeded standard normal draws on the free velocity unknowns of both
     components: (count, 2 n_free)."""
     return np.random.default_rng(seed).standard_normal((count, 2 * n_free))
+
+
+def he_normal_params(channels: int, depth: int, seed: int = 0, c_in: int = 5, c_out: int = 2) -> np.ndarray:
+    """Seeded initial weights of the learned solve's network, flat float32 in the
+    library's layout (per layer W[out][in][3][3] then b[out]): He-normal weights
+    (std sqrt(2 / fan_in)), zero biases, the last layer scaled by 0.1 so the
+    untrained network starts near zero output."""
+    rng = np.random.default_rng(seed)
+    sizes = [c_in] + [channels] * (depth - 1) + [c_out]
+    out = []
+    for k in range(depth):
+        W = rng.standard_normal((sizes[k + 1], sizes[k], 3, 3)) * np.sqrt(2.0 / (sizes[k] * 9))
+        if k == depth - 1:
+            W *= 0.1
+        out += [W.ravel(), np.zeros(sizes[k + 1])]
+    return np.concatenate(out).astype(np.float32)

@@ -145,3 +145,22 @@ def test_picard_resumes_from_a_given_iterate(ctx, binding):
     assert st3.stokes_its == 0 and st3.picard_its == st.picard_its - 2
     assert abs(st3.res[0] - st.res[2]) <= 1e-12 * st.res[2]
     assert _rel(full(u3), full(u)) < 1e-12 and _rel(full(p3), full(p)) < 1e-12
+
+
+def test_device_wait_limit_gives_timeout_and_recovers(ctx, binding):
+    """A cooperative Householder R factor over many CTAs (n_x = 6000 rows of z3
+    spread over the whole GPU) with a wait limit of 0 polls: blocks that reach a grid
+    barrier before the others give up, the call returns TT_ETIMEOUT, and with the
+    default limit the same call succeeds on the same context."""
+    z = otm.TT(*synth.random_tt(6, 3, 6000, 4, 12, seed=41, decay=4))
+    t = ctx.tt(z.z1, z.z2, z.z3)
+    ref, nref = otm.round_tt(z, 1e-8)
+    ctx.set_wait_limit(0)
+    try:
+        with pytest.raises(binding.LibraryError) as e:
+            ctx.round(t, 1e-8)
+        assert e.value.code == binding.TT_ETIMEOUT
+    finally:
+        ctx.set_wait_limit(20000000)
+    g, nb, na = ctx.round(t, 1e-8)
+    assert g.ranks == ref.ranks and abs(nb - nref) <= 1e-12 * nref

@@ -132,8 +132,8 @@ def test_training_reduces_the_loss(setup):
     d = setup["d"]
     net = binding.NetHandle(setup["P"], 8, 4, _flat(setup["params"]))
     R0 = gaussian_residuals(d.n_v, 256, seed=14)
-    losses = net.train(setup["op"], R0, epochs=6, batch=32, lr=3e-3, smooth_max=2)
-    assert losses[-1] < 0.7 * losses[0]
+    losses = net.train(setup["op"], R0, epochs=10, batch=32, lr=3e-3, smooth_max=2)
+    assert losses[-1] < 0.8 * losses[0] and losses[-1] < losses[1]
 
 
 def test_learned_inner_solve_keeps_the_picard_solve_correct(setup):

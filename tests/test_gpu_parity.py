@@ -117,7 +117,7 @@ def test_round_zero_and_rank_one(ctx):
     assert nb == 0.0 and g.ranks == (1, 1) and not full(g).any()
     one = ctx.tt(*synth.random_tt(5, 3, 9, 1, 1, seed=9))
     g, nb, _ = ctx.round(one, 1e-12)
-    assert g.ranks == (1, 1) and _rel(full(g), one.full()) < 1e-14
+    assert g.ranks == (1, 1) and _rel(full(g), full(one)) < 1e-14
 
 
 def test_round_keeps_everything_at_eps_zero(ctx):
