@@ -228,7 +228,8 @@ enum {
                              preconditioned by eq. (11_prec) */
     TT_PREC_LEARNED = 1,  /* the same, with the spatial factor K^-1 of eq. (11_prec)
                              replaced by a trained network (tt_net); an inner solve that
-                             misses tol_inner with it is redone with the exact K^-1 */
+                             misses tol_inner with it within max(4, maxit_inner / 5)
+                             iterations is redone with the exact K^-1 */
     TT_PREC_PCD = 2       /* mean-based PCD, eq. (mean_pcd): not built (TT_EINVAL) */
 };
 
@@ -269,6 +270,11 @@ int tt_net_create(tt_ctx* ctx, const tt_problem* prob, int channels, int depth, 
                   tt_net** out);
 int tt_net_destroy(tt_net* net);
 int tt_net_info(const tt_net* net, int* nparams, int* nx, int* ny);
+/* on != 0 (the default): convolutions with a multiple of 16 (<= 256) output
+ * channels run on the tensor cores as implicit GEMMs with BF16 activations and
+ * weights and FP32 accumulation; 0: every convolution on CUDA cores with FP32
+ * activations (BF16 weights, FP32 accumulation). */
+int tt_net_set_tensor_cores(tt_net* net, int on);
 /* Current FP32 parameters (layout as in tt_net_create) into params (host). */
 int tt_net_get_params(tt_ctx* ctx, const tt_net* net, float* params);
 

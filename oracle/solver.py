@@ -181,8 +181,9 @@ class MeanLSC:
         rhs, _ = round_tt(add((1.0, au), (-1.0, kron_apply(None, None, d.Bt, p))), self.eps)
         A = lambda z: d.apply_mean(self.w, z)
         if self.learned_minv is not None:
+            # the learned attempt gets a fifth of the inner budget (at least 4 iterations)
             u, st = gmres(A, self.learned_minv, rhs, tol=self.tol_inner, eps=self.eps,
-                          maxit=self.maxit_inner, space=_Single)
+                          maxit=min(self.maxit_inner, max(4, self.maxit_inner // 5)), space=_Single)
             if st["res"][-1] <= self.tol_inner * st["bnorm"]:
                 self.inner_its.append(st["its"])
                 return (u, p)

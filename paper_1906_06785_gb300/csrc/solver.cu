@@ -203,10 +203,13 @@ Vec LSCPrec::apply(const Vec& v) {
     tt_ctx* cc = c;
     const VecOp apply_mean = [o, cc](const Vec& x) { Vec y; op_apply_mean(cc, o, x.u.get(), &y.u); return y; };
     if (net) {
+        // the learned attempt gets a fifth of the inner budget (at least 4 iterations):
+        // a network that does not reach tol_inner by then hands over to the exact M^-1
         const tt_net* nn = net;
+        const int maxit_learned = std::max(4, maxit_inner / 5);
         Vec u = gmres(
             c, apply_mean, [cc, nn, o](const Vec& x) { Vec y; y.u = learned_minv(cc, nn, o, x.u.get()); return y; },
-            b, tol_inner, eps, maxit_inner, 0.0, &go);
+            b, tol_inner, eps, std::min(maxit_inner, maxit_learned), 0.0, &go);
         inner_its += go.its;
         if (go.converged) {
             r.u = std::move(u.u);
