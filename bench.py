@@ -44,6 +44,8 @@ DESCR = {
     "small": "small: step L=5 elem 1/4 (n_u=1312 n_p=209) m=2 d=2 n_xi=6 n_t=20 tau=0.1 nu0=1/50 sigma=0.1 eps=1e-6",
     "medium": "medium: step L=5 elem 1/8 (n_u=5440 n_p=769) m=3 d=3 n_xi=20 n_t=100 tau=0.05 nu0=1/100 "
               "sigma=0.2 eps=1e-5",
+    "large": "large: step L=5 elem 1/16 (n_u=22144 n_p=2945) m=5 d=3 n_xi=56 n_t=400 tau=0.025 nu0=1/200 "
+             "sigma=0.25 eps=1e-5",
 }
 # ncu dram bytes (read + write) per launch of the dominant kernel class, from the
 # capture summarised in profiles/; None until measured for the current kernel.
@@ -66,6 +68,13 @@ def _args():
                     help="1: also train the learned mean-Oseen solve on the GPU and time the solve with it")
     ap.add_argument("--train-pairs", dest="train_pairs", type=int, default=4096)
     ap.add_argument("--train-epochs", dest="train_epochs", type=int, default=3)
+    ap.add_argument("--ops", action="store_true",
+                    help="op-level run on the workload's shapes (default large: n_u=22144, n_xi=56, n_t=400): "
+                         "TT matvec of the full operator and the truncation of its output, per kernel class "
+                         "achieved GB/s and TFLOP/s; prints one JSON line")
+    ap.add_argument("--solves-only", dest="solves_only", action="store_true",
+                    help="profiling run: W warm + K solves of the headline precision and nothing else; prints "
+                         "the kernel launches of each solve (for ncu -s / -c)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="mixed: FP32 SpMM/GEMM/R factors inside GMRES, FP64 SVDs, dots, residual; "
                          "fp64: plain FP64 throughout")
@@ -497,9 +506,100 @@ def run_reference(a):
     print(json.dumps(out), flush=True)
 
 
+def run_ops(a):
+    """TT matvec + truncation at the shapes of a workload, on random trains with
+    prescribed spectra (u ranks (24, 60), p (24, 30), convection field (4, 10)).
+    The matvec is timed without truncation; the truncation T_eps (eps of the
+    workload) of its output separately.  Kernel classes report algorithmic bytes and
+    flops per launch over their event-timed duration."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1906_06785_gb300 import binding
+    wl = a.workload if a.workload != WORKLOAD else "large"
+    prob = synth.preset(wl)
+    ctx = binding.Context()
+    P = ctx.problem(prob)
+    n_t, n_xi = prob.n_t, prob.n_xi
+    zu = synth.random_tt(n_t, n_xi, prob.n_u, 24, 60, seed=42, decay=6)
+    zp = synth.random_tt(n_t, n_xi, prob.n_p, 24, 30, seed=43, decay=6)
+    zw = synth.random_tt(n_t, n_xi, 2 * prob.mesh.n_nodes, 4, 10, seed=44, decay=3)
+    u, p = ctx.tt(*zu), ctx.tt(*zp)
+    w = ctx.tt(zw[0], zw[1], zw[2] * 0.5)
+    op = P.op(w)
+    eps = prob.tol.eps_gmres
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        prof = ctx.prof_read()
+        ctx.profile(False)
+        return sum(ts) / len(ts), prof, out
+
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    fp64 = 152 * 4 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+    def classes(prof, reps):
+        out = {}
+        for k, (n, ms, fl, by) in prof.items():
+            if not n:
+                continue
+            out[k] = {"launches_per_op": n / reps, "ms_per_op": ms / reps, "GB_per_s": by / (ms * 1e-3) / 1e9,
+                      "frac_of_hbm": by / (ms * 1e-3) / 1e9 / hbm, "TFLOP_per_s": fl / (ms * 1e-3) / 1e12}
+        return out
+
+    reps = max(1, a.steps)
+    t_mv, prof_mv, (ou, opp) = timed(lambda: op.matvec(u, p), reps)
+    t_rd, prof_rd, (ru, _, _) = timed(lambda: ctx.round(ou, eps), reps)
+    out = {"mode": "ops", "workload": DESCR.get(wl, wl), "data": "synthetic random trains with prescribed spectra",
+           "input_ranks": {"u": u.ranks, "p": p.ranks, "w": w.ranks}, "matvec_out_ranks": ou.ranks,
+           "rounded_ranks": ru.ranks, "eps": eps, "reps": reps,
+           "matvec_ms": t_mv, "round_ms": t_rd, "matvec_classes": classes(prof_mv, reps),
+           "round_classes": classes(prof_rd, reps),
+           "peaks": {"hbm_gbs": hbm, "fp64_tflops": fp64,
+                     "source": "hbm: MEASURED_PEAKS.json (burst copy); fp64: unit counts x max SM clock"}}
+    print(json.dumps(out), flush=True)
+
+
+def run_solves_only(a):
+    """W + K solves of the workload at the headline precision, nothing else, so that
+    an ncu launch list can skip the warm solves (-s) and cover one solve (-c)."""
+    import torch
+    import synth
+    from paper_1906_06785_gb300 import binding
+    prob = synth.preset(a.workload)
+    ctx = binding.Context()
+    P = ctx.problem(prob)
+    o = binding.opts_from(prob.tol, precision=binding.MIXED if a.precision == "mixed" else binding.FP64)
+    torch.cuda.synchronize()
+    l0 = ctx.launches
+    for k in range(a.warmup + a.steps):
+        t0 = time.perf_counter()
+        P.picard(o)
+        torch.cuda.synchronize()
+        print(json.dumps({"solve": k, "s": time.perf_counter() - t0, "launches_before": l0,
+                          "launches": ctx.launches - l0}), flush=True)
+        l0 = ctx.launches
+
+
 if __name__ == "__main__":
     args = _args()
-    if args.impl == "reference":
+    if args.ops:
+        run_ops(args)
+    elif args.solves_only:
+        run_solves_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.batch > 0:
         run_batch(args)

@@ -102,6 +102,7 @@ _SIGS = {
     "tt_net_create": (_I, [_P, _P, _I, _I, _FP, C.POINTER(_P)]),
     "tt_net_destroy": (_I, [_P]),
     "tt_net_info": (_I, [_P, _IP, _IP, _IP]),
+    "tt_net_set_tensor_cores": (_I, [_P, _I]),
     "tt_net_get_params": (_I, [_P, _P, _FP]),
     "tt_net_apply": (_I, [_P, _P, _P, _DP, _I, _I, _DP]),
     "tt_net_loss_grad": (_I, [_P, _P, _P, _DP, _DP, _I, _I, _DP, _FP]),
@@ -499,6 +500,9 @@ class NetHandle:
         self.ctx.check(self.ctx.lib.tt_net_create(self.ctx.h, problem.h, channels, depth,
                                                   p.ctypes.data_as(_FP), C.byref(h)))
         self.h = h
+
+    def set_tensor_cores(self, on):
+        self.ctx.check(self.ctx.lib.tt_net_set_tensor_cores(self.h, 1 if on else 0))
 
     def info(self):
         n, nx, ny = _I(), _I(), _I()

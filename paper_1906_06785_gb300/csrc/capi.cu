@@ -58,6 +58,51 @@ int max_cluster_ctas(tt_ctx* c, const void* kernel, int threads, size_t smem) {
     return best;
 }
 
+tt_ctx* side_ctx(tt_ctx* c) {
+    if (c->side) return c->side;
+    tt_ctx* s = new tt_ctx;
+    try {
+        s->device = c->device;
+        s->nsm = c->nsm;
+        s->alloc_fn = c->alloc_fn;
+        s->free_fn = c->free_fn;
+        s->alloc_user = c->alloc_user;
+        s->gram_ok = c->gram_ok;
+        s->wait_limit = c->wait_limit;
+        CUDA_CHECK(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+        CUDA_CHECK(cudaMallocHost(&s->pinned, 4096));
+        CUDA_CHECK(cudaMalloc((void**)&s->dstatus, sizeof(int)));
+        CUDA_CHECK(cudaMalloc((void**)&s->dbarrier, 4 * sizeof(unsigned)));
+        CUDA_CHECK(cudaMemset(s->dstatus, 0, sizeof(int)));
+        CUDA_CHECK(cudaMemset(s->dbarrier, 0, 4 * sizeof(unsigned)));
+        CUDA_CHECK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+        CUDA_CHECK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    } catch (...) {
+        if (s->stream) cudaStreamDestroy(s->stream);
+        if (s->pinned) cudaFreeHost(s->pinned);
+        if (s->dstatus) cudaFree(s->dstatus);
+        if (s->dbarrier) cudaFree(s->dbarrier);
+        delete s;
+        throw;
+    }
+    c->side = s;
+    return s;
+}
+
+void destroy_side(tt_ctx* c) {
+    tt_ctx* s = c->side;
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    cudaStreamDestroy(s->stream);
+    cudaFreeHost(s->pinned);
+    cudaFree(s->dstatus);
+    cudaFree(s->dbarrier);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    delete s;
+    c->side = nullptr;
+}
+
 static cudaEvent_t ev_get(tt_ctx* c) {
     if (!c->pd.pool.empty()) {
         cudaEvent_t e = c->pd.pool.back();
@@ -165,6 +210,7 @@ int tt_ctx_create(void* stream, tt_alloc_fn alloc, tt_free_fn free_fn, void* use
 int tt_ctx_destroy(tt_ctx* c) {
     if (!c) return TT_EINVAL;
     cudaStreamSynchronize(c->stream);
+    destroy_side(c);
     try { prof_resolve(c); } catch (...) {}
     for (auto e : c->pd.pool) cudaEventDestroy(e);
     cudaFreeHost(c->pinned);
@@ -182,6 +228,7 @@ long long tt_ctx_launches(const tt_ctx* c) { return c ? c->launches : -1; }
 int tt_ctx_set_wait_limit(tt_ctx* c, long long polls) {
     if (!c || polls < 0) return TT_EINVAL;
     c->wait_limit = polls;
+    if (c->side) c->side->wait_limit = polls;
     return TT_OK;
 }
 

@@ -95,6 +95,11 @@ struct tt_ctx {
     // with the back-off, far beyond any wait of a healthy launch
     long long wait_limit = 20000000LL;
     double* dprof_flops = nullptr;  // device-counted flops per profiling slot
+    // second context on its own stream (created on first use) on which the pressure
+    // train of a (velocity, pressure) pair is truncated while the velocity train is
+    // truncated here: the two truncations are independent and each uses only a few SMs
+    tt_ctx* side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace tt {
@@ -178,6 +183,10 @@ inline void read_back(tt_ctx* c, const T* dsrc, T* hdst, size_t n) {
 
 // Check the device status word after kernels with bounded waits.
 void check_status(tt_ctx* c);
+
+// The context's side context (see tt_ctx::side), created on first use.
+tt_ctx* side_ctx(tt_ctx* c);
+void destroy_side(tt_ctx* c);
 
 // Records an event pair around the launches in its scope when profiling is on.
 struct ProfScope {

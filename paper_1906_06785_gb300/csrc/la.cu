@@ -15,6 +15,8 @@
 #include <cmath>
 #include <cstdlib>
 
+#include <cooperative_groups.h>
+
 #include "la.cuh"
 
 namespace tt {
@@ -583,6 +585,133 @@ k_jacobi(int m, int mr, int n, int npad, T* W, int ldw, int* flags, int max_swee
 }
 
 
+// One-sided Jacobi on one thread-block cluster with the columns held in distributed
+// shared memory.  Pair slot p (one warp) holds the two columns of pair p of the
+// current round of the circle ordering; after rotating them it writes them straight
+// into the slots that pair them in the next round (a ring shift: slot p's first
+// column goes to slot p-1, its second to slot p+1, at the ends to slot 1's second
+// and to slot P-1's own first; slot 0's second column is the fixed one), in the other
+// CTA's shared memory when the neighbour slot lives there.  Every column carries its
+// squared norm and its index, so a round reads only local shared memory and ends with
+// one hardware cluster barrier; after each sweep the columns are back in their
+// starting slots.  Same rotation, ordering and stopping rule as k_jacobi.
+template <int KV>
+__global__ void __launch_bounds__(512)
+k_jacobi_ring(int m, int n, int P, double* __restrict__ W, int ldw, int* __restrict__ flags, int max_sweeps,
+              double tol, double tiny_rel, const double* __restrict__ frob2, int* __restrict__ sweeps_used) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) double rsm[];
+    const int S = blockDim.x >> 5;                 // slots (warps) per CTA
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int blk = (int)cl.block_rank();
+    const int p = blk * S + w;
+    const int NR = 2 * P - 1;
+    // [buf][slot][col][m] data, [buf][slot][col] norms, [buf][slot][col] indices
+    double* data = rsm;
+    double* nrm = data + (size_t)4 * S * m;
+    int* idx = reinterpret_cast<int*>(nrm + 4 * S);
+    auto D = [&](int buf, int slot, int col) { return data + (((size_t)buf * S + slot) * 2 + col) * m; };
+    auto NI = [&](int buf, int slot, int col) { return ((buf * S + slot) * 2 + col); };
+    const double tiny = tiny_rel * *frob2;
+    if (p < P) {
+        const int ia = p, ib = p == 0 ? NR : NR - p;
+        const int cols[2] = {ia, ib};
+        for (int c2 = 0; c2 < 2; ++c2) {
+            const int ci = cols[c2];
+            double* d = D(0, w, c2);
+            double a = 0.0;
+            for (int i = lane; i < m; i += 32) {
+                const double x = ci < n ? W[(size_t)ci * ldw + i] : 0.0;
+                d[i] = x;
+                a = fma(x, x, a);
+            }
+            a = warp_sum(a);
+            if (lane == 0) {
+                nrm[NI(0, w, c2)] = a;
+                idx[NI(0, w, c2)] = ci;
+            }
+        }
+    }
+    cl.sync();
+    int cur = 0, sw = 0;
+    for (; sw < max_sweeps; ++sw) {
+        int any = 0;
+        for (int r = 0; r < NR; ++r) {
+            const int nxt = cur ^ 1;
+            if (p < P) {
+                const double* da = D(cur, w, 0);
+                const double* db = D(cur, w, 1);
+                double al = nrm[NI(cur, w, 0)], be = nrm[NI(cur, w, 1)];
+                const int ia = idx[NI(cur, w, 0)], ib = idx[NI(cur, w, 1)];
+                double xa[KV], xb[KV];
+#pragma unroll
+                for (int k = 0; k < KV; ++k) {
+                    const int i = lane + 32 * k;
+                    xa[k] = i < m ? da[i] : 0.0;
+                    xb[k] = i < m ? db[i] : 0.0;
+                }
+                if (ia < n && ib < n) {
+                    double ga = 0.0;
+#pragma unroll
+                    for (int k = 0; k < KV; ++k) ga = fma(xa[k], xb[k], ga);
+                    ga = warp_sum(ga);
+                    double cs, sn;
+                    if (jacobi_rotation(al, be, ga, tol, tiny, cs, sn)) {
+                        any = 1;
+                        double na = 0.0, nb = 0.0;
+#pragma unroll
+                        for (int k = 0; k < KV; ++k) {
+                            const double xn = cs * xa[k] - sn * xb[k], yn = sn * xa[k] + cs * xb[k];
+                            xa[k] = xn;
+                            xb[k] = yn;
+                            na = fma(xn, xn, na);
+                            nb = fma(yn, yn, nb);
+                        }
+                        al = warp_sum(na);
+                        be = warp_sum(nb);
+                    }
+                }
+                // destinations in the next round
+                int sa, ca, sb, cb;
+                if (p == 0) { sa = 1; ca = 1; sb = 0; cb = 1; }
+                else if (p == P - 1) { sa = p - 1; ca = 0; sb = p; cb = 0; }
+                else { sa = p - 1; ca = 0; sb = p + 1; cb = 1; }
+                double* pa = cl.map_shared_rank(D(nxt, sa % S, ca), sa / S);
+                double* pb = cl.map_shared_rank(D(nxt, sb % S, cb), sb / S);
+#pragma unroll
+                for (int k = 0; k < KV; ++k) {
+                    const int i = lane + 32 * k;
+                    if (i < m) {
+                        pa[i] = xa[k];
+                        pb[i] = xb[k];
+                    }
+                }
+                if (lane == 0) {
+                    *cl.map_shared_rank(nrm + NI(nxt, sa % S, ca), sa / S) = al;
+                    *cl.map_shared_rank(idx + NI(nxt, sa % S, ca), sa / S) = ia;
+                    *cl.map_shared_rank(nrm + NI(nxt, sb % S, cb), sb / S) = be;
+                    *cl.map_shared_rank(idx + NI(nxt, sb % S, cb), sb / S) = ib;
+                }
+            }
+            cl.sync();
+            cur = nxt;
+        }
+        if (any && lane == 0) flags[sw] = 1;
+        cl.sync();
+        if (__ldcg(flags + sw) == 0) break;
+    }
+    if (p < P) {
+        for (int c2 = 0; c2 < 2; ++c2) {
+            const int ci = idx[NI(cur, w, c2)];
+            if (ci >= n) continue;
+            const double* d = D(cur, w, c2);
+            for (int i = lane; i < m; i += 32) W[(size_t)ci * ldw + i] = d[i];
+        }
+    }
+    if (blk == 0 && threadIdx.x == 0) *sweeps_used = sw;
+}
+
 // One-sided Jacobi of a small m x n matrix held entirely in the shared memory of one
 // CTA: one warp per column pair of a round, block barriers between rounds, the same
 // round-robin order, rotation and stopping rule as k_jacobi.  For matrices this small
@@ -694,15 +823,69 @@ __global__ void k_permute_normalise(int m, int n, const double* __restrict__ W, 
 }
 }  // namespace
 
-// Matrices with at most this many entries take the one-CTA shared-memory Jacobi: a
-// round costs about 1.5 m n cycles on one SM's FP64 pipe, which is below the ~3 us of a
-// cross-CTA round at this size.
+// Which Jacobi kernel: the cluster ring (columns in distributed shared memory, pairs
+// spread over up to 16 SMs) for up to kJacobiRingMaxEntries entries; else the one-CTA
+// shared-memory kernel for tiny matrices (or when no cluster can be formed); else the
+// grid kernel with the columns in global memory.  GB300 issues a warp's FP64
+// instruction over 16 cycles of an SM's FP64 pipe, so rounds are bound by FP64
+// instructions per SM: spreading pairs over SMs beats keeping them on one.
 constexpr long long kJacobiCtaMaxEntries = 4096;
+constexpr long long kJacobiRingMaxEntries = 96 * 1024;
 
 template <typename T>
 static void jacobi_grid(tt_ctx* c, int m, int mr, int n, T* W, int ldw, T tol, double tiny_rel,
                         const double* frob2, int max_sweeps, double* fc, const char* tag) {
     const int npad = n + (n & 1);
+    if constexpr (sizeof(T) == sizeof(double)) {
+        const int P = npad / 2;
+        // one cluster of at most 16 SMs: its FP64 pipes carry a round of (n/2) pairs x 12 m
+        // flops; past about 1e5 entries a grid over more SMs (with its slower barrier)
+        // finishes a round sooner
+        if (mr == m && m <= 512 && P >= 2 && P <= 256 && (long long)m * n <= kJacobiRingMaxEntries) {
+            // one cluster, columns in distributed shared memory
+            auto kern = m <= 128 ? k_jacobi_ring<4> : m <= 256 ? k_jacobi_ring<8> : k_jacobi_ring<16>;
+            int G = 0, S = 0;
+            size_t smem = 0;
+            for (int g : {16, 8}) {
+                S = ceil_div(P, g);
+                if (S > 16) continue;
+                smem = (size_t)4 * S * m * sizeof(double) + (size_t)4 * S * (sizeof(double) + sizeof(int));
+                if (smem > 200 * 1024) continue;
+                CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+                if (max_cluster_ctas(c, (const void*)kern, 32 * S, smem) >= g) {
+                    G = ceil_div(P, S);
+                    break;
+                }
+            }
+            if (G >= 2) {
+                DBuf<int> flags(c, max_sweeps + 1);
+                CUDA_CHECK(cudaMemsetAsync(flags.p, 0, (max_sweeps + 1) * sizeof(int), c->stream));
+                int* sweeps = flags.p + max_sweeps;
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(G);
+                cfg.blockDim = dim3(32 * S);
+                cfg.dynamicSmemBytes = smem;
+                cfg.stream = c->stream;
+                cudaLaunchAttribute attr;
+                attr.id = cudaLaunchAttributeClusterDimension;
+                attr.val.clusterDim.x = G;
+                attr.val.clusterDim.y = 1;
+                attr.val.clusterDim.z = 1;
+                cfg.attrs = &attr;
+                cfg.numAttrs = 1;
+                CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, m, n, P, (double*)W, ldw, flags.p, max_sweeps, (double)tol,
+                                              tiny_rel, frob2, sweeps));
+                count_launch(c);
+                static const bool log = getenv("TT_LOG_ROUND") != nullptr;
+                if (log) {
+                    int h = 0;
+                    read_back(c, (const int*)sweeps, &h, 1);
+                    fprintf(stderr, "jacobi%s-ring m=%d n=%d ctas=%d sweeps=%d\n", tag, m, n, G, h);
+                }
+                return;
+            }
+        }
+    }
     if constexpr (sizeof(T) == sizeof(double)) {
         if ((long long)m * n <= kJacobiCtaMaxEntries && mr == m) {
             // small matrix: one CTA, everything in shared memory

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "solver.cuh"
+#include "umma.cuh"
 
 struct tt_net {
     tt_ctx* c = nullptr;          // context that owns the device buffers
@@ -38,6 +39,9 @@ struct tt_net {
     tt::DBuf<__nv_bfloat16> wflip;// BF16 weights of the transposed convolution [in][out][9]
     tt::DBuf<float> adam_m, adam_v;
     int adam_t = 0;
+    // convolutions with at least 16 output channels run on the tcgen05 tensor cores
+    // (BF16 activations as operands); 0: every convolution on the FP32 CUDA-core kernel
+    int tensor_cores = 1;
 };
 
 namespace tt {
@@ -336,6 +340,10 @@ void refresh_weights(tt_ctx* c, tt_net* net) {
 
 void conv_launch(tt_ctx* c, const tt_net* net, int B, int Cin, int Cout, const float* X, const __nv_bfloat16* W,
                  const float* bias, int relu, const float* gate, float* zout, float* out) {
+    if (net->tensor_cores && conv3x3_umma_ok(Cin, Cout)) {
+        conv3x3_umma(c, B, Cin, Cout, net->nx, net->ny, X, W, bias, relu, gate, zout, out);
+        return;
+    }
     const int tiles = ceil_div(net->nx, TILE) * ceil_div(net->ny, TILE);
     ProfScope prof(c, PROF_CONV, 2.0 * 9 * Cin * Cout * (double)net->npix * B,
                    4.0 * ((double)B * (Cin + Cout * (zout ? 2 : 1)) * net->npix) + 2.0 * 9 * Cin * Cout);
@@ -582,6 +590,12 @@ int tt_net_create(tt_ctx* ctx, const tt_problem* P, int channels, int depth, con
 int tt_net_destroy(tt_net* net) {
     if (!net) return TT_EINVAL;
     delete net;
+    return TT_OK;
+}
+
+int tt_net_set_tensor_cores(tt_net* net, int on) {
+    if (!net) return TT_EINVAL;
+    net->tensor_cores = on ? 1 : 0;
     return TT_OK;
 }
 

@@ -478,8 +478,7 @@ double residual(tt_ctx* c, tt_problem* P, const tt_t* u, const tt_t* p, double e
                           {C3{P->fp, S_COPY, nullptr, 1.0}, C3{u, S_DIV, nullptr, 1.0}},
                           {C2{0, 0, nullptr, 1.0, nullptr}, C2{1, 1, nullptr, -1.0, nullptr}});
     RoundOut a, b;
-    *ru = round_tt(c, rawu.get(), eps, &a);
-    *rp = round_tt(c, rawp.get(), eps, &b);
+    round_pair(c, rawu.get(), rawp.get(), eps, ru, rp, &a, &b);
     return std::hypot(a.nrm_after, b.nrm_after);
 }
 

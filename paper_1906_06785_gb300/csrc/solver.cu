@@ -64,8 +64,8 @@ __global__ void k_lsq(int k, const double* __restrict__ Hbar, int ldh, double be
 static Vec vround(tt_ctx* c, const Vec& v, double eps, double* before, double* after) {
     Vec r;
     RoundOut a, b;
-    r.u = round_tt(c, v.u.get(), eps, &a);
-    if (v.p) r.p = round_tt(c, v.p.get(), eps, &b);
+    if (v.p) round_pair(c, v.u.get(), v.p.get(), eps, &r.u, &r.p, &a, &b);
+    else r.u = round_tt(c, v.u.get(), eps, &a);
     if (before) *before = std::hypot(a.nrm_before, b.nrm_before);
     if (after) *after = std::hypot(a.nrm_after, b.nrm_after);
     return r;

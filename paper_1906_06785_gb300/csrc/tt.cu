@@ -12,6 +12,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <exception>
+#include <thread>
 
 #include "tt.cuh"
 
@@ -355,6 +357,48 @@ TTPtr round_tt(tt_ctx* c, const tt_t* z, double eps, RoundOut* info, int cap1, i
         fprintf(stderr, "round n=(%d,%d,%d) R=(%d,%d) -> (%d,%d) eps=%.1e fast=%d\n", n_t, n_xi, n_x, R1, R2, r1,
                 r2, eps, c->fast);
     return out;
+}
+
+// T_eps of a velocity train and a pressure train at once: the pressure train is
+// truncated on the side context's stream from a second host thread while the
+// velocity train is truncated on the context's own stream (the two truncations
+// share no data; each synchronises its own stream for its ranks).  The results are
+// those of two consecutive round_tt calls; the pressure result is handed back to the
+// context (its memory is released in the context's stream order).
+void round_pair(tt_ctx* c, const tt_t* u, const tt_t* p, double eps, TTPtr* ru, TTPtr* rp, RoundOut* iu,
+                RoundOut* ip) {
+    tt_ctx* s = side_ctx(c);
+    s->fast = c->fast;
+    s->alloc_fn = c->alloc_fn;
+    s->free_fn = c->free_fn;
+    s->alloc_user = c->alloc_user;
+    CUDA_CHECK(cudaEventRecord(c->ev_fork, c->stream));
+    CUDA_CHECK(cudaStreamWaitEvent(s->stream, c->ev_fork, 0));
+    TTPtr outp{nullptr, tt_free};
+    std::exception_ptr perr;
+    std::thread th([&]() {
+        try {
+            CUDA_CHECK(cudaSetDevice(s->device));
+            outp = round_tt(s, p, eps, ip);
+        } catch (...) {
+            perr = std::current_exception();
+        }
+    });
+    std::exception_ptr uerr;
+    try {
+        *ru = round_tt(c, u, eps, iu);
+    } catch (...) {
+        uerr = std::current_exception();
+    }
+    th.join();
+    c->launches += s->launches;
+    s->launches = 0;
+    CUDA_CHECK(cudaEventRecord(c->ev_join, s->stream));
+    CUDA_CHECK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    if (uerr) std::rethrow_exception(uerr);
+    if (perr) std::rethrow_exception(perr);
+    outp->ctx = c;
+    *rp = std::move(outp);
 }
 
 // ============================================================== inner products

@@ -26,6 +26,11 @@ struct RoundOut {
 // singular triplets up to the cap and reports it in info->capped).
 TTPtr round_tt(tt_ctx* c, const tt_t* z, double eps, RoundOut* info = nullptr, int cap1 = 0, int cap2 = 0);
 
+// T_eps of a velocity train u and a pressure train p, the two truncations running
+// concurrently (the pressure one on the context's side stream).
+void round_pair(tt_ctx* c, const tt_t* u, const tt_t* p, double eps, TTPtr* ru, TTPtr* rp, RoundOut* iu,
+                RoundOut* ip);
+
 // <vec a, vec b> written to the device scalar *dout.
 void dot_dev(tt_ctx* c, const tt_t* a, const tt_t* b, double* dout);
 double dot_host(tt_ctx* c, const tt_t* a, const tt_t* b);
