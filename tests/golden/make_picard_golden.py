@@ -1,11 +1,15 @@
-"""Write tests/golden/picard_<preset>.txt from the CPU oracle only.
+"""Write golden records of oracle solves, from the CPU oracle only.
 
-Runs the oracle's truncated inexact Picard iteration (Algorithm 3.1) on a
-preset and stores: the iteration counts, ||u||, ||p||, the final relative
-residual, and the full-tensor values of u and p at 256 seeded index triples
-each.  GPU tests compare against these samples.
-
-    python tests/golden/make_picard_golden.py small
+  python tests/golden/make_picard_golden.py small
+      the oracle's truncated inexact Picard iteration (Algorithm 3.1) on a preset:
+      tests/golden/picard_<preset>.txt (iteration counts, ||u||, ||p||, the final
+      relative residual, the full-tensor values of u and p at 256 seeded index
+      triples) and tests/golden/picard_<preset>_cores.npz (the cores of u and p,
+      for comparisons by TT difference);
+  python tests/golden/make_picard_golden.py medium --stokes
+      the Stokes initial solve of Algorithm 3.1 (TT-GMRES with the mean-based LSC
+      preconditioner, Section 5.2) on a preset: tests/golden/stokes_<preset>.npz
+      (cores, outer and inner iteration counts, ||f||, the truncated residual).
 """
 import os
 import sys
@@ -28,10 +32,31 @@ def entry(t, i, s, j):
     return float(t.z1[i] @ t.z2[:, s, :] @ t.z3[:, j])
 
 
+def stokes(name):
+    import time
+    from oracle.solver import MeanLSC, gmres, _Pair
+    prob = synth.preset(name)
+    d = Discretisation(prob)
+    t = prob.tol
+    fu, fp = d.rhs()
+    fnorm = float(np.hypot(norm(fu), norm(fp)))
+    P = MeanLSC(d, None, t.eps_gmres, t.tol_inner, t.maxit_inner)
+    t0 = time.time()
+    (u, p), st = gmres(lambda v: d.apply(None, *v), P, (fu, fp), tol=t.tol_gmres, eps=t.eps_gmres,
+                       maxit=t.maxit_gmres, space=_Pair, bnorm=fnorm)
+    out = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"stokes_{name}.npz")
+    np.savez_compressed(out, u1=u.z1, u2=u.z2, u3=u.z3, p1=p.z1, p2=p.z2, p3=p.z3, its=st["its"],
+                        inner_its=np.array(P.inner_its), fnorm=fnorm, res=st["res"][-1],
+                        seconds=time.time() - t0)
+    print(out, st["its"], P.inner_its, u.ranks, p.ranks)
+
+
 def main(name):
     prob = synth.preset(name)
     d = Discretisation(prob)
     u, p, st = picard(d)
+    np.savez_compressed(os.path.join(os.path.dirname(os.path.abspath(__file__)), f"picard_{name}_cores.npz"),
+                        u1=u.z1, u2=u.z2, u3=u.z3, p1=p.z1, p2=p.z2, p3=p.z3)
     rng = np.random.default_rng(2024)
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"picard_{name}.txt")
     with open(out, "w") as f:
@@ -54,4 +79,8 @@ def main(name):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1] if len(sys.argv) > 1 else "small")
+    name = sys.argv[1] if len(sys.argv) > 1 else "small"
+    if "--stokes" in sys.argv:
+        stokes(name)
+    else:
+        main(name)

@@ -1,15 +1,15 @@
 """GPU solves at workload sizes against the CPU oracle.
 
-* small workload: the full Picard solve (FP64 and mixed precision) against
-  samples of the oracle's solution stored by tests/golden/make_picard_golden.py;
-* medium workload (the benchmark's): one Kronecker matvec and one truncation of
-  medium-shaped trains, compared with the oracle on sampled entries and by TT
-  differences.
+* small workload: the full Picard solve (FP64 and mixed precision) against the
+  oracle's solution stored by tests/golden/make_picard_golden.py, by relative TT
+  difference ||u - u_oracle|| / ||u_oracle|| (cores stored) and on sampled entries;
+* medium workload (the mixed-precision workload): the Stokes initial solve of
+  Algorithm 3.1 against the oracle's by TT difference, one Kronecker matvec and
+  one truncation of medium-shaped trains.
 
-Tolerances: FP64 path 1e-6 relative (sample error / largest sampled magnitude),
-mixed path 1e-4; matvec 1e-12 (same arithmetic, different summation order);
-truncation 1e-10 on inputs whose spectra keep every singular value away from
-the cut.
+Tolerances: FP64 path 1e-6 relative, mixed path 1e-4 (the targets of the method);
+matvec 1e-12 (same arithmetic, different summation order); truncation 1e-10 on
+inputs whose spectra keep every singular value away from the cut.
 """
 import os
 
@@ -68,8 +68,36 @@ def test_small_picard_matches_oracle(ctx, mixed, tol):
     assert st.res[st.picard_its] <= prob.tol.tol_picard * st.fnorm
     assert _sample_err(u, g["u"]) < tol
     assert _sample_err(p, g["p"]) < tol
+    c = np.load(os.path.join(GOLD, "picard_small_cores.npz"))
+    assert _tt_rel(u, otm.TT(c["u1"], c["u2"], c["u3"])) < tol
+    assert _tt_rel(p, otm.TT(c["p1"], c["p2"], c["p3"])) < tol
     if not mixed:
         assert st.picard_its == g["picard_its"]
+
+
+def _tt_rel(h, ref):
+    """||h - ref|| / ||ref|| by concatenation and orthogonalisation (oracle arithmetic)."""
+    return otm.norm(otm.add((1.0, otm.TT(*h.cores())), (-1.0, ref))) / otm.norm(ref)
+
+
+@pytest.mark.parametrize("mixed,tol", [(0, 1e-6), (1, 1e-4)])
+def test_medium_stokes_solve_matches_oracle(ctx, mixed, tol):
+    """The Stokes solve that starts Algorithm 3.1 on the medium workload: TT-GMRES with
+    the mean-based LSC preconditioner and its inner solves, outer and inner iteration
+    counts and the solution against the oracle's."""
+    from paper_1906_06785_gb300 import binding
+    c = np.load(os.path.join(GOLD, "stokes_medium.npz"))
+    prob = synth.preset("medium")
+    P = ctx.problem(prob)
+    fu, fp = P.rhs()
+    o = binding.opts_from(prob.tol, precision=mixed)
+    u, p, st, code = P.op(None).gmres(o, fu, fp, float(c["fnorm"]))
+    assert code == binding.TT_OK
+    assert st.its == int(c["its"])
+    if not mixed:
+        assert st.inner_its == int(c["inner_its"].sum())
+    assert _tt_rel(u, otm.TT(c["u1"], c["u2"], c["u3"])) < tol
+    assert _tt_rel(p, otm.TT(c["p1"], c["p2"], c["p3"])) < tol
 
 
 def _medium_pair(ctx, d, seed):
