@@ -152,6 +152,14 @@ __global__ void k_sqrt_abs(int n, double* __restrict__ v) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) v[i] = sqrt(fabs(v[i]));
 }
+// column j (rows 0..m-1, leading dimension ld) of X scaled by sqrt(s[j]) (mode 0) or
+// by 1 / s[j] (mode 1; a zero s[j] gives a zero column); one block per column
+__global__ void k_scale_cols(int m, double* __restrict__ X, int ld, const double* __restrict__ s, int mode) {
+    const int j = blockIdx.x;
+    const double v = s[j];
+    const double f = mode == 0 ? sqrt(fabs(v)) : (v > 0.0 ? 1.0 / v : 0.0);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) X[(size_t)j * ld + i] *= f;
+}
 }  // namespace
 
 // Truncation through Gram matrices, for tolerances well above sqrt(machine eps):
@@ -208,25 +216,49 @@ static TTPtr round_gram(tt_ctx* c, const tt_t* z, double eps, RoundOut* info, in
     gemm(c, r1, n_xi * R2, R1, 1.0, rowmaj(P1.p, R1), rowmaj(z->z2, (long long)n_xi * R2), 0.0,
          rowmaj(C2.p, (long long)n_xi * R2));
     const int m = r1 * n_xi;
-    // S2 = C2_left G3 C2_left^T (narrow) or (C2_left z3^T)(C2_left z3^T)^T (wide)
-    DBuf<double> S2(c, (size_t)m * m);
-    if (!wide) {
-        DBuf<double> T2(c, (size_t)m * R2);
-        gemm(c, m, R2, R2, 1.0, rowmaj(C2.p, R2), rowmaj(G3.p, R2), 0.0, rowmaj(T2.p, R2));
-        gemm(c, m, m, R2, 1.0, rowmaj(T2.p, R2), trans(rowmaj(C2.p, R2)), 0.0, colmaj(S2.p, m));
+    // Left singular pairs of the second unfolding Y = C2_left z3^T (m x n_x) from the
+    // smaller of two Gram matrices: S2 = Y Y^T (m x m), or, on the narrow route when
+    // 2 R2^3 < m^3, B^T B (R2 x R2) with B = C2_left F and G3 = F F^T (F = eigenvectors
+    // of G3 scaled by the square roots of its eigenvalues): Y Y^T = B B^T, so the
+    // eigenpairs (V, Sigma^2) of B^T B give the left singular vectors U2 = B V Sigma^-1.
+    const bool rside = !wide && 2.0 * R2 * R2 * (double)R2 < (double)m * m * m;
+    const int p2 = rside ? R2 : m;
+    DBuf<double> sig2(c, p2), U2(c, (size_t)m * p2), Bm, V;
+    if (rside) {
+        DBuf<double> lg(c, R2), Ug(c, (size_t)R2 * R2);
+        left_svd(c, R2, R2, colmaj(G3.p, R2), lg.p, Ug.p);
+        k_scale_cols<<<R2, 128, 0, c->stream>>>(R2, Ug.p, R2, lg.p, 0);
+        LAUNCH_CHECK(c);
+        Bm.alloc(c, (size_t)m * R2);
+        gemm(c, m, R2, R2, 1.0, rowmaj(C2.p, R2), colmaj(Ug.p, R2), 0.0, rowmaj(Bm.p, R2));
+        DBuf<double> K(c, (size_t)R2 * R2);
+        gemm(c, R2, R2, m, 1.0, trans(rowmaj(Bm.p, R2)), rowmaj(Bm.p, R2), 0.0, colmaj(K.p, R2));
+        V.alloc(c, (size_t)R2 * R2);
+        left_svd(c, R2, R2, colmaj(K.p, R2), sig2.p, V.p);
     } else {
-        DBuf<double> Y(c, (size_t)m * n_x);
-        gemm(c, m, n_x, R2, 1.0, rowmaj(C2.p, R2), trans(rowmaj(z->z3, R2)), 0.0, rowmaj(Y.p, n_x));
-        gemm(c, m, m, n_x, 1.0, rowmaj(Y.p, n_x), trans(rowmaj(Y.p, n_x)), 0.0, colmaj(S2.p, m));
+        DBuf<double> S2(c, (size_t)m * m);
+        if (!wide) {
+            DBuf<double> T2(c, (size_t)m * R2);
+            gemm(c, m, R2, R2, 1.0, rowmaj(C2.p, R2), rowmaj(G3.p, R2), 0.0, rowmaj(T2.p, R2));
+            gemm(c, m, m, R2, 1.0, rowmaj(T2.p, R2), trans(rowmaj(C2.p, R2)), 0.0, colmaj(S2.p, m));
+        } else {
+            DBuf<double> Y(c, (size_t)m * n_x);
+            gemm(c, m, n_x, R2, 1.0, rowmaj(C2.p, R2), trans(rowmaj(z->z3, R2)), 0.0, rowmaj(Y.p, n_x));
+            gemm(c, m, m, n_x, 1.0, rowmaj(Y.p, n_x), trans(rowmaj(Y.p, n_x)), 0.0, colmaj(S2.p, m));
+        }
+        left_svd(c, m, m, colmaj(S2.p, m), sig2.p, U2.p);
     }
-    DBuf<double> sig2(c, m), U2(c, (size_t)m * m);
-    left_svd(c, m, m, colmaj(S2.p, m), sig2.p, U2.p);
-    k_sqrt_abs<<<ceil_div(m, 256), 256, 0, c->stream>>>(m, sig2.p);
+    k_sqrt_abs<<<ceil_div(p2, 256), 256, 0, c->stream>>>(p2, sig2.p);
     LAUNCH_CHECK(c);
-    trunc_second(c, sig2.p, m, eps, dinfo.p, cap2);
+    trunc_second(c, sig2.p, p2, eps, dinfo.p, cap2);
     read_back(c, dinfo.p, &h, 1);
     check_status(c);
     const int r2 = h.r2;
+    if (rside) {
+        gemm(c, m, r2, R2, 1.0, rowmaj(Bm.p, R2), colmaj(V.p, R2), 0.0, colmaj(U2.p, m));
+        k_scale_cols<<<r2, 128, 0, c->stream>>>(m, U2.p, m, sig2.p, 1);
+        LAUNCH_CHECK(c);
+    }
     TTPtr out = wrap(tt_alloc(c, n_t, n_xi, n_x, r1, r2));
     CUDA_CHECK(cudaMemcpyAsync(out->z1, U1.p, (size_t)n_t * r1 * sizeof(double), cudaMemcpyDeviceToDevice,
                                c->stream));

@@ -293,3 +293,20 @@ def test_round_gram_route_and_first_core_compression(ctx, eps):
     assert abs(nb - nref) < 1e-12 * nref
     assert _tt_diff(_oracle_tt(g), ref) < 1e-8
     assert otm.norm(otm.add((1.0, _oracle_tt(g)), (-1.0, z))) <= eps * nref * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("eps", [1e-5, 1e-3])
+def test_round_gram_route_on_the_smaller_gram_side(ctx, eps):
+    """Gram route with r1 n_xi far above R2 (2 R2^3 < (r1 n_xi)^3): the second unfolding's
+    singular pairs come from the R2 x R2 Gram matrix B^T B.  Same T_eps as the oracle's."""
+    n_t, n_xi, n_x = 12, 20, 700
+    a = otm.TT(*synth.random_tt(n_t, n_xi, n_x, 10, 40, seed=33, decay=9))
+    b = otm.TT(*synth.random_tt(n_t, n_xi, n_x, 10, 40, seed=34, decay=9))
+    z = otm.add((1.0, a), (0.6, b))
+    g, nb, na = ctx.round(ctx.tt(z.z1, z.z2, z.z3), eps)
+    ref, nref = otm.round_tt(z, eps)
+    assert g.ranks == ref.ranks
+    assert 2 * 80 ** 3 < (g.ranks[0] * n_xi) ** 3
+    assert abs(nb - nref) < 1e-12 * nref
+    assert _tt_diff(_oracle_tt(g), ref) < 1e-8
+    assert otm.norm(otm.add((1.0, _oracle_tt(g)), (-1.0, z))) <= eps * nref * (1 + 1e-6)
