@@ -80,11 +80,16 @@ def _tt_rel(h, ref):
     return otm.norm(otm.add((1.0, otm.TT(*h.cores())), (-1.0, ref))) / otm.norm(ref)
 
 
-@pytest.mark.parametrize("mixed,tol", [(0, 1e-6), (1, 1e-4)])
+@pytest.mark.parametrize("mixed,tol", [(0, 1e-5), (1, 1e-4)])
 def test_medium_stokes_solve_matches_oracle(ctx, mixed, tol):
     """The Stokes solve that starts Algorithm 3.1 on the medium workload: TT-GMRES with
     the mean-based LSC preconditioner and its inner solves, outer and inner iteration
-    counts and the solution against the oracle's."""
+    counts and the solution against the oracle's.  Every vector of this solve is
+    truncated at eps_gmres = 1e-5, and on the FP64 path the GPU takes the Gram route
+    (singular values from eigenvalues of Gram matrices, absolute error ~ n eps_mach
+    ||z||^2 next to delta^2 = eps^2 ||z||^2 / 2), so singular triplets near the cut are
+    fixed only to O(eps) and two correct implementations agree to eps_gmres, not to
+    rounding: the FP64 tolerance is eps_gmres (measured: 2e-6)."""
     from paper_1906_06785_gb300 import binding
     c = np.load(os.path.join(GOLD, "stokes_medium.npz"))
     prob = synth.preset("medium")
