@@ -72,6 +72,10 @@ def _args():
                     help="op-level run on the workload's shapes (default large: n_u=22144, n_xi=56, n_t=400): "
                          "TT matvec of the full operator and the truncation of its output, per kernel class "
                          "achieved GB/s and TFLOP/s; prints one JSON line")
+    ap.add_argument("--study", default="", choices=["", "table53", "sweep"],
+                    help="table53: the paper problem (Table 5.1) with the three GMRES tolerances of Table 5.3; "
+                         "sweep: the paper problem over element sizes h and time steps tau (Fig. 5.6); one JSON "
+                         "line per solve")
     ap.add_argument("--solves-only", dest="solves_only", action="store_true",
                     help="profiling run: W warm + K solves of the headline precision and nothing else; prints "
                          "the kernel launches of each solve (for ncu -s / -c)")
@@ -572,6 +576,52 @@ def run_ops(a):
     print(json.dumps(out), flush=True)
 
 
+def run_study(a):
+    """Solver studies on the paper's own problem (Table 5.1: symmetric step L = 12,
+    h = 1/4, n_t = 64, tau = 1/64, nu0 = 1/50, sigma = 0.01, b = 4, m = 3, d = 3) with the
+    Table 5.2 tolerances, FP64 and the LSC preconditioner as in the paper:
+      table53: tol_gmres in {1e-1, 1e-3, 1e-5} with eps_gmres = 1e-2 tol_gmres (Table 5.3);
+      sweep:   element size h in {1/2, 1/4, 1/8} at n_t = 64, and n_t in {16, 32, 64, 128}
+               (tau = 1 / n_t) at h = 1/4 (Fig. 5.6).
+    Each solve is timed once with CUDA events (after a warm-up solve of the first case)."""
+    import torch
+    import synth
+    from paper_1906_06785_gb300 import binding
+    ctx = binding.Context()
+    stream = torch.cuda.current_stream()
+    if a.study == "table53":
+        cases = [dict(label=f"tol_gmres={tg:g}", over={}, tol=dict(tol_gmres=tg, eps_gmres=1e-2 * tg))
+                 for tg in (1e-1, 1e-3, 1e-5)]
+    else:
+        cases = [dict(label=f"h={h:g}", over=dict(h=h), tol={}) for h in (0.5, 0.25, 0.125)]
+        cases += [dict(label=f"n_t={nt}", over=dict(n_t=nt, tau=1.0 / nt), tol={}) for nt in (16, 32, 64, 128)]
+    warm = True
+    for cs in cases:
+        prob = synth.preset("paper", **cs["over"])
+        for k, v in cs["tol"].items():
+            setattr(prob.tol, k, v)
+        P = ctx.problem(prob)
+        o = binding.opts_from(prob.tol, precision=binding.FP64)
+        if warm:
+            P.picard(o)
+            warm = False
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        u, p, st, code = P.picard(o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        n = st.picard_its
+        print(json.dumps({"study": a.study, "case": cs["label"], "n_u": prob.n_u, "n_p": prob.n_p,
+                          "n_xi": prob.n_xi, "n_t": prob.n_t, "h_element": prob.params["h"],
+                          "tol_gmres": prob.tol.tol_gmres, "eps_gmres": prob.tol.eps_gmres, "status": int(code),
+                          "picard_its": n, "gmres_its_total": int(sum(st.gmres_its[1:n + 1])),
+                          "gmres_its": list(st.gmres_its[1:n + 1]), "stokes_its": st.stokes_its,
+                          "rel_res": st.res[n] / st.fnorm, "u_ranks": u.ranks, "p_ranks": p.ranks,
+                          "seconds": e0.elapsed_time(e1) / 1000.0}), flush=True)
+        del u, p, P
+
+
 def run_solves_only(a):
     """W + K solves of the workload at the headline precision, nothing else, so that
     an ncu launch list can skip the warm solves (-s) and cover one solve (-c)."""
@@ -595,7 +645,9 @@ def run_solves_only(a):
 
 if __name__ == "__main__":
     args = _args()
-    if args.ops:
+    if args.study:
+        run_study(args)
+    elif args.ops:
         run_ops(args)
     elif args.solves_only:
         run_solves_only(args)

@@ -128,6 +128,19 @@ int tt_round(tt_ctx* ctx, const tt_t* in, double eps, tt_t** out,
 int tt_round_to(tt_ctx* ctx, const tt_t* in, double eps, tt_t* out, double* norm_before,
                 double* norm_after);
 
+/* Randomized T_eps (an opt-in variant of Section 4.1's truncation): when the second
+ * rank exceeds 256, a Gaussian sketch (Khatri-Rao test matrix over time and gPC modes,
+ * counter-based draws from `seed`) of the second unfolding's row space replaces the
+ * last core by an orthonormal basis of ell columns, ell = max(128, R2 / 4) doubling
+ * until 8 Gaussian probes estimate the energy the basis misses below 0.1% of
+ * eps^2 ||z||^2; the deterministic T_eps then truncates the small train with the budget
+ * that is left.  The bound ||T(z) - z|| <= eps ||z|| then holds with high probability;
+ * ranks can differ from tt_round's by the rank-decision noise.  Smaller ranks, or a
+ * sketch that would not be narrower than R2, take tt_round.  sketch (may be NULL):
+ * the width used (R2 when deterministic). */
+int tt_round_randomized(tt_ctx* ctx, const tt_t* in, double eps, unsigned long long seed, tt_t** out,
+                        double* norm_before, double* norm_after, int* sketch);
+
 /* <vec a, vec b> (Section 4.1) into *out (host). */
 int tt_dot(tt_ctx* ctx, const tt_t* a, const tt_t* b, double* out);
 
@@ -317,6 +330,7 @@ int tt_residual(tt_ctx* ctx, tt_problem* prob, const tt_t* u, const tt_t* p, dou
 /* ---- solvers (Algorithms 4.2, 3.1) ----------------------------------------- */
 
 enum { TT_FP64 = 0, TT_MIXED = 1 };
+enum { TT_ROUND_EXACT = 0, TT_ROUND_RANDOMIZED = 1 };
 
 typedef struct {
     double tol_picard;   /* Picard stopping ||r|| <= tol_picard ||f|| */
@@ -337,6 +351,9 @@ typedef struct {
     const tt_t* init_u;     /* non-NULL (with init_p): start Algorithm 3.1 from this
                                iterate instead of the Stokes solve (resume a solve) */
     const tt_t* init_p;
+    int rounding;           /* TT_ROUND_EXACT: every truncation by T_eps; TT_ROUND_RANDOMIZED:
+                               the truncations inside GMRES (and the preconditioner) by
+                               tt_round_randomized, the Picard-level ones exact */
 } tt_solver_opts;
 
 typedef struct {

@@ -20,6 +20,7 @@ TT_OK, TT_EINVAL, TT_ENOMEM, TT_ECUDA, TT_ENOCONV, TT_ERANK, TT_ENAN, TT_ETIMEOU
 OP_FULL, OP_MEAN = 0, 1
 PREC_LSC, PREC_LEARNED, PREC_PCD = 0, 1, 2
 FP64, MIXED = 0, 1
+ROUND_EXACT, ROUND_RANDOMIZED = 0, 1
 F64 = 0
 MAX_PICARD = 64
 
@@ -41,7 +42,8 @@ class ProblemDesc(C.Structure):
 class SolverOpts(C.Structure):
     _fields_ = [("tol_picard", _D), ("tol_gmres", _D), ("eps_gmres", _D), ("eps_soln", _D),
                 ("eps_conv", _D), ("tol_inner", _D), ("maxit_picard", _I), ("maxit_gmres", _I),
-                ("maxit_inner", _I), ("precision", _I), ("learned", _P), ("init_u", _P), ("init_p", _P)]
+                ("maxit_inner", _I), ("precision", _I), ("learned", _P), ("init_u", _P), ("init_p", _P),
+                ("rounding", _I)]
 
 
 class PrecOpts(C.Structure):
@@ -83,6 +85,7 @@ _SIGS = {
     "tt_get_cores": (_I, [_P, _P, _P, _P, _P, _I]),
     "tt_round": (_I, [_P, _P, _D, C.POINTER(_P), _DP, _DP]),
     "tt_round_to": (_I, [_P, _P, _D, _P, _DP, _DP]),
+    "tt_round_randomized": (_I, [_P, _P, _D, C.c_ulonglong, C.POINTER(_P), _DP, _DP, _IP]),
     "tt_dot": (_I, [_P, _P, _P, _DP]),
     "tt_norm": (_I, [_P, _P, _DP]),
     "tt_dot_noalloc": (_I, [_P, _P, _P, _DP]),
@@ -236,6 +239,13 @@ class Context:
         out = _P(); nb = _D(); na = _D()
         self.check(self.lib.tt_round(self.h, t.h, eps, C.byref(out), C.byref(nb), C.byref(na)))
         return TTHandle(self, out), nb.value, na.value
+
+    def round_randomized(self, t, eps, seed=1):
+        """Randomized T_eps: (train, ||t||, ||T(t)||, sketch width)."""
+        out = _P(); nb = _D(); na = _D(); sk = _I()
+        self.check(self.lib.tt_round_randomized(self.h, t.h, eps, seed, C.byref(out), C.byref(nb), C.byref(na),
+                                                C.byref(sk)))
+        return TTHandle(self, out), nb.value, na.value, sk.value
 
     def round_to(self, t, eps, out):
         """T_eps(t) into the existing train `out`; returns (status, ||t||, ||T(t)||),

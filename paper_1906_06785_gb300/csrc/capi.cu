@@ -338,6 +338,18 @@ int tt_round_to(tt_ctx* ctx, const tt_t* in, double eps, tt_t* out, double* nb, 
     API_END
 }
 
+int tt_round_randomized(tt_ctx* ctx, const tt_t* in, double eps, unsigned long long seed, tt_t** out, double* nb,
+                        double* na, int* sketch) {
+    API_BEGIN(ctx)
+    TT_REQUIRE(ctx && in && out, "null argument");
+    RoundOut info;
+    TTPtr r = round_rand(ctx, in, eps, seed, &info, sketch);
+    if (nb) *nb = info.nrm_before;
+    if (na) *na = info.nrm_after;
+    *out = r.release();
+    API_END
+}
+
 int tt_dot(tt_ctx* ctx, const tt_t* a, const tt_t* b, double* out) {
     API_BEGIN(ctx)
     TT_REQUIRE(ctx && a && b && out, "null argument");
@@ -539,7 +551,10 @@ int tt_gmres(tt_ctx* ctx, tt_op* op, tt_prec* prec, const tt_solver_opts* o, con
     b.p = clone(ctx, bp);
     GmresOut go;
     tt_ctx* c = ctx;
+    TT_REQUIRE(o->rounding == TT_ROUND_EXACT || o->rounding == TT_ROUND_RANDOMIZED, "unknown rounding %d",
+               o->rounding);
     PrecScope ps(ctx, o->precision == TT_MIXED ? 1 : 0);
+    RandScope rs(ctx, o->rounding == TT_ROUND_RANDOMIZED);
     Vec z = gmres(
         ctx, [c, op](const Vec& x) { Vec y; op_apply(c, op, x.u.get(), x.p.get(), &y.u, &y.p); return y; },
         [&pre](const Vec& v) { return pre.apply(v); }, b, o->tol_gmres, o->eps_gmres, o->maxit_gmres, bnorm, &go);

@@ -73,6 +73,10 @@ struct tt_ctx {
     // (with their R factors), inner products, Hessenberg solves and band
     // factorisations are FP64 always.
     int fast = 0;
+    // Truncations inside GMRES take the randomized variant (round_rand) when set; the
+    // sketches draw from a counter-based generator at seed rand_seq, advanced per call
+    bool randomized = false;
+    unsigned long long rand_seq = 0x243F6A8885A308D3ull;
     // Truncations with eps >= 5e-6 may take the Gram route (FP64 GEMMs and
     // eigenpairs of small Gram matrices instead of Householder R factors).
     bool gram_ok = true;
@@ -197,6 +201,14 @@ struct ProfScope {
     ~ProfScope();
 };
 void prof_resolve(tt_ctx* c);
+
+// Sets whether GMRES truncations are randomized for its scope (restores on exit).
+struct RandScope {
+    tt_ctx* c;
+    bool saved;
+    RandScope(tt_ctx* ctx, bool on) : c(ctx), saved(ctx->randomized) { c->randomized = on; }
+    ~RandScope() { c->randomized = saved; }
+};
 
 // Sets the context's compute precision for its scope (restores on exit).
 struct PrecScope {

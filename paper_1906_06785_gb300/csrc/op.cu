@@ -435,6 +435,7 @@ void op_apply_mean(tt_ctx* c, const tt_op* op, const tt_t* u, TTPtr* ou) {
 // ============================================================== residual
 double residual(tt_ctx* c, tt_problem* P, const tt_t* u, const tt_t* p, double eps, TTPtr* ru, TTPtr* rp) {
     PrecScope fp64(c, 0);   // the Picard residual is FP64 in every precision mode
+    RandScope exact(c, false);   // and its truncation deterministic
     const double ti = 1.0 / P->tau;
     const int m1 = P->m + 1;
     const size_t nnz = P->ff.nnz, nnzD = std::max(1, P->fD.nnz), nxi2 = (size_t)P->n_xi * P->n_xi;

@@ -65,7 +65,7 @@ static Vec vround(tt_ctx* c, const Vec& v, double eps, double* before, double* a
     Vec r;
     RoundOut a, b;
     if (v.p) round_pair(c, v.u.get(), v.p.get(), eps, &r.u, &r.p, &a, &b);
-    else r.u = round_tt(c, v.u.get(), eps, &a);
+    else r.u = round_any(c, v.u.get(), eps, &a);
     if (before) *before = std::hypot(a.nrm_before, b.nrm_before);
     if (after) *after = std::hypot(a.nrm_after, b.nrm_after);
     return r;
@@ -183,7 +183,7 @@ TTPtr LSCPrec::schur(const tt_t* ap) {
     y = apply_space(c, P, y.get(), S_MSTARINV);
     TTPtr my{nullptr, tt_free};
     op_apply_mean(c, op, y.get(), &my);
-    y = round_tt(c, my.get(), eps);
+    y = round_any(c, my.get(), eps);
     y = apply_space(c, P, y.get(), S_MSTARINV);
     y = apply_space(c, P, y.get(), S_DIV);
     return apply_space(c, P, y.get(), S_SOLVE_LP, -1.0);
@@ -194,7 +194,7 @@ Vec LSCPrec::apply(const Vec& v) {
     Vec r;
     r.p = schur(v.p.get());
     TTPtr bt = apply_space(c, P, r.p.get(), S_GRAD);
-    TTPtr rhs = round_tt(c, concat(c, {Summand{1.0, nullptr, v.u.get()}, Summand{-1.0, nullptr, bt.get()}}).get(), eps);
+    TTPtr rhs = round_any(c, concat(c, {Summand{1.0, nullptr, v.u.get()}, Summand{-1.0, nullptr, bt.get()}}).get(), eps);
     // (F_0 + C) u = rhs by inner low-rank GMRES preconditioned with M (Section 5.3)
     Vec b;
     b.u = std::move(rhs);
@@ -237,6 +237,8 @@ static VecOp full_op(tt_ctx* c, tt_op* op) {
 void picard(tt_ctx* c, tt_problem* P, const tt_solver_opts* o, TTPtr* uo, TTPtr* po, tt_picard_stats* st) {
     TT_REQUIRE(o, "null options");
     TT_REQUIRE(o->precision == TT_FP64 || o->precision == TT_MIXED, "unknown precision %d", o->precision);
+    TT_REQUIRE(o->rounding == TT_ROUND_EXACT || o->rounding == TT_ROUND_RANDOMIZED, "unknown rounding %d",
+               o->rounding);
     TT_REQUIRE((o->init_u == nullptr) == (o->init_p == nullptr), "init_u and init_p go together");
     memset(st, 0, sizeof(*st));
     st->fnorm = P->fnorm;
@@ -261,6 +263,7 @@ void picard(tt_ctx* c, tt_problem* P, const tt_solver_opts* o, TTPtr* uo, TTPtr*
         Vec up;
         {
             PrecScope ps(c, fast);
+            RandScope rs(c, o->rounding == TT_ROUND_RANDOMIZED);
             up = gmres(c, full_op(c, &stokes), [&pre](const Vec& v) { return pre.apply(v); }, f, o->tol_gmres,
                        o->eps_gmres, o->maxit_gmres, P->fnorm, &go);
         }
@@ -292,6 +295,7 @@ void picard(tt_ctx* c, tt_problem* P, const tt_solver_opts* o, TTPtr* uo, TTPtr*
         GmresOut go;
         {
             PrecScope ps(c, fast);
+            RandScope rs(c, o->rounding == TT_ROUND_RANDOMIZED);
             d = gmres(c, full_op(c, &L), [&pr](const Vec& v) { return pr.apply(v); }, r, o->tol_gmres,
                       o->eps_gmres, o->maxit_gmres, rn, &go);
         }

@@ -397,10 +397,20 @@ TTPtr round_tt(tt_ctx* c, const tt_t* z, double eps, RoundOut* info, int cap1, i
 // share no data; each synchronises its own stream for its ranks).  The results are
 // those of two consecutive round_tt calls; the pressure result is handed back to the
 // context (its memory is released in the context's stream order).
+TTPtr round_any(tt_ctx* c, const tt_t* z, double eps, RoundOut* info) {
+    if (!c->randomized) return round_tt(c, z, eps, info);
+    const unsigned long long seed = c->rand_seq;
+    c->rand_seq = c->rand_seq * 6364136223846793005ull + 1442695040888963407ull;
+    return round_rand(c, z, eps, seed, info);
+}
+
 void round_pair(tt_ctx* c, const tt_t* u, const tt_t* p, double eps, TTPtr* ru, TTPtr* rp, RoundOut* iu,
                 RoundOut* ip) {
     tt_ctx* s = side_ctx(c);
     s->fast = c->fast;
+    s->randomized = c->randomized;
+    s->rand_seq = c->rand_seq ^ 0x9E3779B97F4A7C15ull;
+    c->rand_seq = c->rand_seq * 6364136223846793005ull + 1442695040888963407ull;
     s->alloc_fn = c->alloc_fn;
     s->free_fn = c->free_fn;
     s->alloc_user = c->alloc_user;
@@ -411,14 +421,14 @@ void round_pair(tt_ctx* c, const tt_t* u, const tt_t* p, double eps, TTPtr* ru, 
     std::thread th([&]() {
         try {
             CUDA_CHECK(cudaSetDevice(s->device));
-            outp = round_tt(s, p, eps, ip);
+            outp = round_any(s, p, eps, ip);
         } catch (...) {
             perr = std::current_exception();
         }
     });
     std::exception_ptr uerr;
     try {
-        *ru = round_tt(c, u, eps, iu);
+        *ru = round_any(c, u, eps, iu);
     } catch (...) {
         uerr = std::current_exception();
     }

@@ -26,10 +26,22 @@ struct RoundOut {
 // singular triplets up to the cap and reports it in info->capped).
 TTPtr round_tt(tt_ctx* c, const tt_t* z, double eps, RoundOut* info = nullptr, int cap1 = 0, int cap2 = 0);
 
+// T_eps by round_rand when the context's randomized flag is set, else round_tt.
+TTPtr round_any(tt_ctx* c, const tt_t* z, double eps, RoundOut* info = nullptr);
+
 // T_eps of a velocity train u and a pressure train p, the two truncations running
 // concurrently (the pressure one on the context's side stream).
 void round_pair(tt_ctx* c, const tt_t* u, const tt_t* p, double eps, TTPtr* ru, TTPtr* rp, RoundOut* iu,
                 RoundOut* ip);
+
+// Randomized T_eps (rround.cu): trains whose second rank exceeds kRandMinRank are first
+// compressed by a Gaussian sketch of ell columns (ell doubling until probes estimate the
+// missed energy below 0.1% of eps^2 ||z||^2), then truncated deterministically; smaller
+// trains, and sketches that would not be narrower than R2, take round_tt.  seed selects
+// the draws; ell_used (may be null) reports the sketch width (R2: deterministic).
+constexpr int kRandMinRank = 256;
+TTPtr round_rand(tt_ctx* c, const tt_t* z, double eps, uint64_t seed, RoundOut* info = nullptr,
+                 int* ell_used = nullptr);
 
 // <vec a, vec b> written to the device scalar *dout.
 void dot_dev(tt_ctx* c, const tt_t* a, const tt_t* b, double* dout);
