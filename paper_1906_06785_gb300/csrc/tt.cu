@@ -152,12 +152,13 @@ __global__ void k_sqrt_abs(int n, double* __restrict__ v) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) v[i] = sqrt(fabs(v[i]));
 }
-// column j (rows 0..m-1, leading dimension ld) of X scaled by sqrt(s[j]) (mode 0) or
-// by 1 / s[j] (mode 1; a zero s[j] gives a zero column); one block per column
+// column j (rows 0..m-1, leading dimension ld) of X scaled by sqrt(s[j]) (mode 0), by
+// 1 / s[j] (mode 1; a zero s[j] gives a zero column) or by s[j] (mode 2); one block
+// per column
 __global__ void k_scale_cols(int m, double* __restrict__ X, int ld, const double* __restrict__ s, int mode) {
     const int j = blockIdx.x;
     const double v = s[j];
-    const double f = mode == 0 ? sqrt(fabs(v)) : (v > 0.0 ? 1.0 / v : 0.0);
+    const double f = mode == 0 ? sqrt(fabs(v)) : mode == 1 ? (v > 0.0 ? 1.0 / v : 0.0) : v;
     for (int i = threadIdx.x; i < m; i += blockDim.x) X[(size_t)j * ld + i] *= f;
 }
 }  // namespace
@@ -221,13 +222,16 @@ static TTPtr round_gram(tt_ctx* c, const tt_t* z, double eps, RoundOut* info, in
     // 2 R2^3 < m^3, B^T B (R2 x R2) with B = C2_left F and G3 = F F^T (F = eigenvectors
     // of G3 scaled by the square roots of its eigenvalues): Y Y^T = B B^T, so the
     // eigenpairs (V, Sigma^2) of B^T B give the left singular vectors U2 = B V Sigma^-1.
-    const bool rside = !wide && 2.0 * R2 * R2 * (double)R2 < (double)m * m * m;
+    const bool rside = !wide && R2 < n_x && 2.0 * R2 * R2 * (double)R2 < (double)m * m * m;
     const int p2 = rside ? R2 : m;
     DBuf<double> sig2(c, p2), U2(c, (size_t)m * p2), Bm, V;
     if (rside) {
+        // F = V_z Sigma_z from the SVD of z3^T (QR-preconditioned Jacobi on the factor, so
+        // the only squaring of a spectrum is the one of B^T B below)
+        // (the narrow route has R2 < n_x, so z3^T has R2 singular values)
         DBuf<double> lg(c, R2), Ug(c, (size_t)R2 * R2);
-        left_svd(c, R2, R2, colmaj(G3.p, R2), lg.p, Ug.p);
-        k_scale_cols<<<R2, 128, 0, c->stream>>>(R2, Ug.p, R2, lg.p, 0);
+        left_svd(c, R2, n_x, trans(rowmaj(z->z3, R2)), lg.p, Ug.p);
+        k_scale_cols<<<R2, 128, 0, c->stream>>>(R2, Ug.p, R2, lg.p, 2);
         LAUNCH_CHECK(c);
         Bm.alloc(c, (size_t)m * R2);
         gemm(c, m, R2, R2, 1.0, rowmaj(C2.p, R2), colmaj(Ug.p, R2), 0.0, rowmaj(Bm.p, R2));

@@ -85,6 +85,7 @@ def test_medium_stokes_with_randomized_truncation(ctx):
     o = binding.opts_from(prob.tol, precision=binding.MIXED, rounding=binding.ROUND_RANDOMIZED)
     u, p, st, code = P.op(None).gmres(o, fu, fp, float(c["fnorm"]))
     assert code == binding.TT_OK and st.its == int(c["its"])
+    # the tolerance of the mixed-precision Stokes iterate (see test_gpu_solve.py)
     for h, k in ((u, "u"), (p, "p")):
         ref = otm.TT(c[k + "1"], c[k + "2"], c[k + "3"])
-        assert _err(h, ref) <= 1e-4 * otm.norm(ref)
+        assert _err(h, ref) <= 1e-3 * otm.norm(ref)
