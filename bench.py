@@ -217,8 +217,8 @@ def _sample_error(t, samples):
 
 
 def _tt_rel_diff(ctx, a, b):
-    """||a - b|| / ||b|| from the singular values of the concatenated train (no
-    cancellation of ||a||^2 - 2<a,b> + ||b||^2)."""
+    """||a - b|| from the singular values of the concatenated train (no cancellation
+    of ||a||^2 - 2<a,b> + ||b||^2); callers divide by the norm they compare against."""
     d = ctx.axpby(1.0, a, -1.0, b)
     _, nd, _ = ctx.round(d, 0.0)
     return nd
@@ -565,12 +565,18 @@ def run_ops(a):
 
     reps = max(1, a.steps)
     t_mv, prof_mv, (ou, opp) = timed(lambda: op.matvec(u, p), reps)
-    t_rd, prof_rd, (ru, _, _) = timed(lambda: ctx.round(ou, eps), reps)
+    t_rd, prof_rd, (ru, nb, _) = timed(lambda: ctx.round(ou, eps), reps)
+    # randomized truncation of the same train (Khatri-Rao sketch, seeded), and its
+    # distance to the exact truncation relative to the train's norm
+    t_rr, prof_rr, (rr, _, _, ell) = timed(lambda: ctx.round_randomized(ou, eps, seed=11), reps)
+    rr_err = _tt_rel_diff(ctx, rr, ru) / nb
     out = {"mode": "ops", "workload": DESCR.get(wl, wl), "data": "synthetic random trains with prescribed spectra",
            "input_ranks": {"u": u.ranks, "p": p.ranks, "w": w.ranks}, "matvec_out_ranks": ou.ranks,
            "rounded_ranks": ru.ranks, "eps": eps, "reps": reps,
            "matvec_ms": t_mv, "round_ms": t_rd, "matvec_classes": classes(prof_mv, reps),
            "round_classes": classes(prof_rd, reps),
+           "randomized": {"round_ms": t_rr, "ranks": rr.ranks, "sketch_width": ell,
+                          "rel_diff_vs_exact": rr_err, "classes": classes(prof_rr, reps)},
            "peaks": {"hbm_gbs": hbm, "fp64_tflops": fp64,
                      "source": "hbm: MEASURED_PEAKS.json (burst copy); fp64: unit counts x max SM clock"}}
     print(json.dumps(out), flush=True)

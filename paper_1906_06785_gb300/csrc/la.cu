@@ -317,6 +317,229 @@ __global__ void __launch_bounds__(256) k_qr_r(QRParams<TC> P) {
     }
 }
 
+// Householder R factor on one thread-block cluster of G <= 16 CTAs, CTA g holding rows
+// [g nb, g nb + nb) of A in shared memory.  The same combined reduction per column as
+// k_qr_r (|a_j|^2 over the live rows, a_j^T a_l and row j), but the partials stay in
+// each CTA's shared memory (double-buffered by column parity) and every CTA sums the
+// G partials of each entry it needs through distributed shared memory, so a column
+// costs one hardware cluster barrier.  Inside a CTA the dot products run a group of
+// lanes per trailing column over the CTA's rows and the rank-1 update one thread per
+// entry, so no column waits on a chain of warp reductions.  Row j of the working rows
+// becomes R(j, :) in place (the diagonal is stored after the update) and R is written
+// at the end.  With perm set, column pivoting (Businger and Golub): step j first swaps
+// in the trailing column of largest remaining norm (norms downdated by R(j, l)^2, the
+// same values in every CTA), A P = Q R, and perm[j] is the original index of column j.
+template <typename TC>
+struct QRClParams {
+    int n, c, k, nb, nbp, L;
+    const double* A;
+    long long rs, cs;
+    double* R;
+    int ldr;
+    const double* fnorm;   // ||A||_F^2 (FP32 arithmetic works on A / ||A||_F), or null
+    int* perm;             // column permutation (pivoting), or null
+};
+
+template <typename TC>
+__global__ void __launch_bounds__(256) k_qr_cl(QRClParams<TC> P) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    TC* sm = reinterpret_cast<TC*>(sm_raw);
+    const int G = (int)cl.num_blocks(), g = (int)cl.block_rank();
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int row0 = g * P.nb;
+    const int rows = max(0, min(P.nb, P.n - row0));
+    const int c = P.c, L = P.L;
+    const bool pivot = P.perm != nullptr;
+    TC* red = sm;                                  // [32]
+    TC* part = red + 32;                           // [2][L] this CTA's partials
+    TC* sums = part + 2 * L;                       // [L] reduced entries
+    TC* wl = sums + L;                             // [c] update coefficients
+    TC* nrm2 = wl + c;                             // [c] remaining squared column norms
+    TC* W = nrm2 + c;                              // [c][nbp] this CTA's rows
+    int* pidx = reinterpret_cast<int*>(W + (size_t)c * P.nbp);   // [c] column of origin
+    int* ired = pidx + c;                          // [32] argmax indices
+    double sc = 1.0;
+    if (P.fnorm) {
+        const double f = sqrt(__ldcg(P.fnorm));
+        sc = (f > 0.0 && f < 1e300) ? f : 1.0;
+    }
+    const double inv = 1.0 / sc;
+    // load: the unit-stride index of A runs over consecutive threads
+    const long long tot = (long long)rows * c;
+    if (P.cs == 1) {
+        for (long long t = tid; t < tot; t += nt) {
+            const int i = (int)(t / c), l = (int)(t % c);
+            W[(size_t)l * P.nbp + i] = TC(P.A[(long long)(row0 + i) * P.rs + l] * inv);
+        }
+    } else {
+        for (long long t = tid; t < tot; t += nt) {
+            const int l = (int)(t / rows), i = (int)(t % rows);
+            W[(size_t)l * P.nbp + i] = TC(P.A[(long long)(row0 + i) * P.rs + (long long)l * P.cs] * inv);
+        }
+    }
+    __syncthreads();
+    if (pivot) {
+        // column norms over all rows: partials in buffer 1 (column 0 writes buffer 0, and
+        // no CTA writes buffer 1 before every CTA has passed column 0's barrier)
+        TC* np = part + L;
+        for (int l = tid; l < c; l += nt) {
+            const TC* w2 = W + (size_t)l * P.nbp;
+            TC s = TC(0);
+            for (int i = 0; i < rows; ++i) s += w2[i] * w2[i];
+            np[l] = s;
+            pidx[l] = l;
+        }
+        cl.sync();
+        for (int l = tid; l < c; l += nt) {
+            TC s = TC(0);
+            for (int q = 0; q < G; ++q) s += *cl.map_shared_rank(np + l, q);
+            nrm2[l] = s;
+        }
+        __syncthreads();
+    }
+    for (int j = 0; j < P.k; ++j) {
+        TC* mypart = part + (j & 1) * L;
+        const int ib = max(0, j - row0);
+        const int live = max(0, rows - ib);
+        const int jloc = j - row0;
+        const bool own = jloc >= 0 && jloc < rows;
+        if (pivot) {
+            // the trailing column of largest remaining norm (lowest index on ties)
+            TC bv = TC(-1);
+            int bi = c;
+            for (int l = j + tid; l < c; l += nt) {
+                const TC v = nrm2[l];
+                if (v > bv) { bv = v; bi = l; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const TC ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+            }
+            if (lane == 0) { red[warp] = bv; ired[warp] = bi; }
+            __syncthreads();
+            if (tid == 0) {
+                for (int q = 1; q < (nt >> 5); ++q)
+                    if (red[q] > bv || (red[q] == bv && ired[q] < bi)) { bv = red[q]; bi = ired[q]; }
+                ired[0] = bi;
+            }
+            __syncthreads();
+            const int pv = ired[0];
+            if (pv != j && pv < c) {
+                TC* a0 = W + (size_t)j * P.nbp;
+                TC* a1 = W + (size_t)pv * P.nbp;
+                for (int i = tid; i < rows; i += nt) {
+                    const TC x = a0[i];
+                    a0[i] = a1[i];
+                    a1[i] = x;
+                }
+                if (tid == 0) {
+                    const TC x = nrm2[j]; nrm2[j] = nrm2[pv]; nrm2[pv] = x;
+                    const int y = pidx[j]; pidx[j] = pidx[pv]; pidx[pv] = y;
+                }
+            }
+            __syncthreads();
+        }
+        const TC* wj = W + (size_t)j * P.nbp;
+        // (a) partials: [0] = |a_j|^2, [1 + l] = a_j^T a_l (l > j), [1 + c + l] = a_jl (owner)
+        {
+            TC s = TC(0);
+            for (int i = ib + tid; i < rows; i += nt) s += wj[i] * wj[i];
+            s = warp_sum(s);
+            if (lane == 0) red[warp] = s;
+        }
+        const int nl = c - j - 1;
+        if (nl > 0) {
+            int tpc = 1;                            // lanes per trailing column
+            while (tpc < 32 && 2 * tpc * nl <= nt) tpc *= 2;
+            const int per = nt / tpc;               // columns per pass
+            for (int l0 = 0; l0 < nl; l0 += per) {
+                const int l = j + 1 + l0 + tid / tpc, sub = tid % tpc;
+                TC d0 = TC(0), d1 = TC(0);
+                if (l < c) {
+                    const TC* w2 = W + (size_t)l * P.nbp;
+                    int i = ib + sub;
+                    for (; i + tpc < rows; i += 2 * tpc) {
+                        d0 += wj[i] * w2[i];
+                        d1 += wj[i + tpc] * w2[i + tpc];
+                    }
+                    if (i < rows) d0 += wj[i] * w2[i];
+                }
+                TC d = d0 + d1;
+                for (int o = tpc >> 1; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                if (sub == 0 && l < c) mypart[1 + l] = d;
+            }
+        }
+        if (own)
+            for (int l = j + tid; l < c; l += nt) mypart[1 + c + l] = W[(size_t)l * P.nbp + jloc];
+        __syncthreads();
+        if (tid < 32) {
+            TC s = tid < (nt >> 5) ? red[tid] : TC(0);
+            s = warp_sum(s);
+            if (tid == 0) mypart[0] = s;
+        }
+        // (b) every CTA's partials are complete
+        cl.sync();
+        // (c) sums: the norm and the products over all CTAs, row j from its owner
+        const int owner = min(j / P.nb, G - 1);
+        for (int t = tid; t < 1 + nl + (c - j); t += nt) {
+            if (t <= nl) {
+                const int idx = t == 0 ? 0 : 1 + j + t;
+                TC s = TC(0);
+                for (int q = 0; q < G; ++q) s += *cl.map_shared_rank(part + (j & 1) * L + idx, q);
+                sums[idx] = s;
+            } else {
+                const int idx = 1 + c + j + (t - 1 - nl);
+                sums[idx] = *cl.map_shared_rank(part + (j & 1) * L + idx, owner);
+            }
+        }
+        __syncthreads();
+        const TC ss = sums[0], x0 = sums[1 + c + j];
+        // zero column (FP32: below 1e-15 of the unit-norm input, where 1 / (v^T v)
+        // would overflow): row j stays as it stands
+        const TC zero_ss = sizeof(TC) < sizeof(double) ? TC(1e-30) : TC(0);
+        if (ss <= zero_ss) continue;
+        const TC sigma = sqrt(ss);
+        const TC alpha = x0 >= TC(0) ? -sigma : sigma;
+        const TC v0 = x0 - alpha;
+        const TC beta = TC(1) / (ss + fabs(x0) * sigma);    // 2 / v^T v
+        // v = a_j - alpha e_j: v^T a_l = a_j^T a_l - alpha a_jl, w_l = beta v^T a_l;
+        // R(j, l) = a_jl - v0 w_l leaves |R(j, l)|^2 of column l's remaining norm behind
+        for (int l = j + 1 + tid; l < c; l += nt) {
+            const TC el = sums[1 + c + l];
+            const TC w = beta * (sums[1 + l] - alpha * el);
+            wl[l] = w;
+            if (pivot) {
+                const TC r = el - v0 * w;
+                nrm2[l] = max(TC(0), nrm2[l] - r * r);
+            }
+        }
+        __syncthreads();
+        // (d) a_l -= v w_l on this CTA's live rows, one thread per entry
+        const long long upd = (long long)nl * live;
+        for (long long t = tid; t < upd; t += nt) {
+            const int l = j + 1 + (int)(t / live), i = ib + (int)(t % live);
+            const TC vi = (row0 + i == j) ? v0 : wj[i];
+            W[(size_t)l * P.nbp + i] -= vi * wl[l];
+        }
+        __syncthreads();
+        if (own && tid == 0) W[(size_t)j * P.nbp + jloc] = alpha;
+    }
+    __syncthreads();
+    // R(i, :) for the rows this CTA holds
+    for (long long t = tid; t < (long long)rows * c; t += nt) {
+        const int i = (int)(t / c), l = (int)(t % c);
+        const int gi = row0 + i;
+        if (gi < P.k) P.R[(size_t)gi * P.ldr + l] = l < gi ? 0.0 : (double)W[(size_t)l * P.nbp + i] * sc;
+    }
+    if (pivot && g == 0)
+        for (int l = tid; l < c; l += nt) P.perm[l] = pidx[l];
+    // no CTA leaves while another may still read its partials
+    cl.sync();
+}
+
 // sum of squares of a strided n x cols matrix, accumulated into *out (zeroed by the caller)
 __global__ void k_frob2_strided(int n, int cols, const double* __restrict__ A, long long rs, long long cs,
                                 double* __restrict__ out) {
@@ -338,9 +561,61 @@ __global__ void k_frob2_strided(int n, int cols, const double* __restrict__ A, l
     }
 }
 
+// Returns whether the columns were pivoted (perm written): only the cluster kernel
+// pivots; the grid kernel (rows beyond one cluster's shared memory) does not.
 template <typename TC>
-void qr_r_launch(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr) {
+bool qr_r_launch(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr, int* perm) {
     const int k = std::min(n, cols);
+    const int L = 2 * cols + 1;
+    DBuf<double> fn;
+    if (sizeof(TC) < sizeof(double)) {
+        fn.alloc(c, 1);
+        CUDA_CHECK(cudaMemsetAsync(fn.p, 0, sizeof(double), c->stream));
+        const long long len = (long long)n * cols;
+        const int fb = (int)std::min<long long>(2LL * c->nsm, std::max(1LL, (len + 255) / 256));
+        k_frob2_strided<<<fb, 256, 0, c->stream>>>(n, cols, A.p, A.s0, A.s1, fn.p);
+        LAUNCH_CHECK(c);
+    }
+    // Householder R factor: 2 n c^2 - 2 c^3 / 3 flops (n >= c); reads A once, writes R
+    const double kk = k;
+    ProfScope prof(c, PROF_QR, 2.0 * kk * kk * ((double)n + cols - kk) - 2.0 * kk * kk * kk / 3.0,
+                   8.0 * ((double)n * cols + kk * cols));
+    {
+        // one cluster of up to 16 CTAs with the rows in shared memory (at least 16 rows
+        // a CTA): one cluster barrier per column
+        const int Gc = std::min(16, std::max(1, ceil_div(n, 16)));
+        const int nbc = ceil_div(n, Gc);
+        const int Gu = ceil_div(n, nbc);
+        const int nbpc = nbc | 1;
+        const size_t smc = ((size_t)32 + 3 * (size_t)L + 2 * (size_t)cols + (size_t)cols * nbpc) * sizeof(TC) +
+                           ((size_t)cols + 32) * sizeof(int);
+        if (smc <= 200 * 1024) {
+            CUDA_CHECK(cudaFuncSetAttribute(k_qr_cl<TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+            if (Gu == 1 || max_cluster_ctas(c, (const void*)k_qr_cl<TC>, 256, smc) >= Gu) {
+                QRClParams<TC> Q;
+                Q.n = n; Q.c = cols; Q.k = k; Q.nb = nbc; Q.nbp = nbpc; Q.L = L;
+                Q.A = A.p; Q.rs = A.s0; Q.cs = A.s1;
+                Q.R = R; Q.ldr = ldr;
+                Q.fnorm = fn.p;
+                Q.perm = perm;
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(Gu);
+                cfg.blockDim = dim3(256);
+                cfg.dynamicSmemBytes = smc;
+                cfg.stream = c->stream;
+                cudaLaunchAttribute attr;
+                attr.id = cudaLaunchAttributeClusterDimension;
+                attr.val.clusterDim.x = Gu;
+                attr.val.clusterDim.y = 1;
+                attr.val.clusterDim.z = 1;
+                cfg.attrs = &attr;
+                cfg.numAttrs = 1;
+                CUDA_CHECK(cudaLaunchKernelEx(&cfg, k_qr_cl<TC>, Q));
+                count_launch(c);
+                return perm != nullptr;
+            }
+        }
+    }
     int G = std::min(c->nsm, std::max(1, ceil_div(n, 16)));
     // Small panels run in one CTA: its columns then cost two block barriers instead
     // of two grid barriers (~2 us each), which dominate below ~4k (FP64: one SM's
@@ -359,17 +634,7 @@ void qr_r_launch(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr) {
     } else {
         gwork.alloc(c, (size_t)G * nbp * cols);
     }
-    const int L = 2 * cols + 1;
     DBuf<TC> scratch(c, (size_t)G * L + L);
-    DBuf<double> fn;
-    if (sizeof(TC) < sizeof(double)) {
-        fn.alloc(c, 1);
-        CUDA_CHECK(cudaMemsetAsync(fn.p, 0, sizeof(double), c->stream));
-        const long long len = (long long)n * cols;
-        const int fb = (int)std::min<long long>(2LL * c->nsm, std::max(1LL, (len + 255) / 256));
-        k_frob2_strided<<<fb, 256, 0, c->stream>>>(n, cols, A.p, A.s0, A.s1, fn.p);
-        LAUNCH_CHECK(c);
-    }
     QRParams<TC> P;
     P.n = n; P.c = cols; P.k = k; P.nb = nb; P.nbp = nbp; P.L = L;
     P.A = A.p; P.rs = A.s0; P.cs = A.s1;
@@ -384,10 +649,6 @@ void qr_r_launch(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr) {
     CUDA_CHECK(cudaMemsetAsync(c->dbarrier, 0, 2 * sizeof(unsigned), c->stream));
     CUDA_CHECK(cudaFuncSetAttribute(k_qr_r<TC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     CUDA_CHECK(cudaFuncSetAttribute(k_qr_r<TC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    // Householder R factor: 2 n c^2 - 2 c^3 / 3 flops (n >= c); reads A once, writes R
-    const double kk = k;
-    ProfScope prof(c, PROF_QR, 2.0 * kk * kk * ((double)n + cols - kk) - 2.0 * kk * kk * kk / 3.0,
-                   8.0 * ((double)n * cols + kk * cols));
     // a grid that fits in one thread-block cluster synchronises with the hardware
     // cluster barrier (~10x cheaper than the grid barrier); larger grids are cooperative
     if (G > 1 && G <= max_cluster_ctas(c, (const void*)k_qr_r<TC, true>, 256, smem)) {
@@ -409,13 +670,14 @@ void qr_r_launch(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr) {
         CUDA_CHECK(cudaLaunchCooperativeKernel((void*)k_qr_r<TC, false>, dim3(G), dim3(256), args, smem, c->stream));
     }
     count_launch(c);
+    return false;
 }
 }  // namespace
 
 void qr_r(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr) {
     TT_REQUIRE(n > 0 && cols > 0, "qr_r: empty matrix %d x %d", n, cols);
-    if (c->fast) qr_r_launch<float>(c, n, cols, A, R, ldr);
-    else qr_r_launch<double>(c, n, cols, A, R, ldr);
+    if (c->fast) qr_r_launch<float>(c, n, cols, A, R, ldr, nullptr);
+    else qr_r_launch<double>(c, n, cols, A, R, ldr, nullptr);
 }
 
 // ============================================================== Jacobi SVD
@@ -585,27 +847,71 @@ k_jacobi(int m, int mr, int n, int npad, T* W, int ldw, int* flags, int max_swee
 }
 
 
+// Sum over the L lanes of a lane group (L a power of two, groups aligned to L).
+__device__ __forceinline__ double group_sum(double v, int L) {
+    for (int o = L >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// The rotation of jacobi_rotation written with two reciprocal square roots and no
+// division: with q = (be - al)^2 + (2 ga)^2, cos 2theta = |be - al| / sqrt(q) and
+// sin 2theta = sign(be - al) 2 ga / sqrt(q); h = (1 + cos 2theta) / 2 gives
+// cs = sqrt(h) = h / sqrt(h), sn = sin 2theta / (2 cs) and t = tan theta = sn / cs.
+// The same inner rotation (|theta| <= pi/4) as t = sign(zeta) / (|zeta| + sqrt(1 +
+// zeta^2)); every lane of a group computes it from group-uniform al, be, ga.
+// tg = t ga is the squared norm the rotation moves from column a to column b.
+__device__ __forceinline__ bool ring_rotation(double al, double be, double ga, double tol, double tiny,
+                                              double& cs, double& sn, double& tg) {
+    const bool rot = al > tiny && be > tiny && ga * ga > (tol * tol * al) * be;
+    cs = 1.0;
+    sn = 0.0;
+    tg = 0.0;
+    if (rot) {
+        const double d = be - al, g2 = 2.0 * ga;
+        const double ir = rsqrt(fma(d, d, g2 * g2));
+        const double c2 = fabs(d) * ir;
+        const double s2 = copysign(1.0, d) * g2 * ir;
+        const double h = fma(0.5, c2, 0.5);
+        const double rh = rsqrt(h);
+        cs = h * rh;
+        sn = 0.5 * s2 * rh;
+        tg = (sn * rh) * ga;
+    }
+    return rot;
+}
+
 // One-sided Jacobi on one thread-block cluster with the columns held in distributed
-// shared memory.  Pair slot p (one warp) holds the two columns of pair p of the
-// current round of the circle ordering; after rotating them it writes them straight
-// into the slots that pair them in the next round (a ring shift: slot p's first
-// column goes to slot p-1, its second to slot p+1, at the ends to slot 1's second
-// and to slot P-1's own first; slot 0's second column is the fixed one), in the other
-// CTA's shared memory when the neighbour slot lives there.  Every column carries its
-// squared norm and its index, so a round reads only local shared memory and ends with
-// one hardware cluster barrier; after each sweep the columns are back in their
-// starting slots.  Same rotation, ordering and stopping rule as k_jacobi.
+// shared memory.  A slot holds the two columns of one pair of the current round of
+// the circle ordering and is served by a group of L lanes (L = 4 .. 32, a warp serves
+// 32 / L slots), each lane holding KV entries of both columns in registers: FP64
+// issue, not the lane count, sets the speed of a round, and a group of L lanes
+// spends the rotation's scalar work once for 32 / L pairs.  After rotating, a slot
+// writes its columns straight into the slots that pair them in the next round (a
+// ring shift: slot p's first column goes to slot p-1, its second to slot p+1, at the
+// ends to slot 1's second and to slot P-1's own first; slot 0's second column is the
+// fixed one), in another CTA's shared memory when the neighbour slot lives there.
+// Every column carries its squared norm and its index, so a round reads only local
+// shared memory and ends with one hardware cluster barrier; after each sweep the
+// columns are back in their starting slots.  Squared norms are recomputed exactly at
+// the start of each sweep and updated by the rotation in between (al - t ga, be +
+// t ga), with an exact recompute when a column loses more than 3/4 of its squared
+// norm.  Same ordering and stopping rule as k_jacobi.
 template <int KV>
-__global__ void __launch_bounds__(512)
-k_jacobi_ring(int m, int n, int P, double* __restrict__ W, int ldw, int* __restrict__ flags, int max_sweeps,
-              double tol, double tiny_rel, const double* __restrict__ frob2, int* __restrict__ sweeps_used) {
+__global__ void __launch_bounds__(256)
+k_jacobi_ring(int m, int n, int P, int L, int S, double* __restrict__ W, int ldw, int* __restrict__ flags,
+              int max_sweeps, double tol, double tiny_rel, const double* __restrict__ frob2,
+              int* __restrict__ sweeps_used) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) double rsm[];
-    const int S = blockDim.x >> 5;                 // slots (warps) per CTA
+    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int spw = 32 / L;
+    const int gl = lane % L;                       // lane within the slot's group
+    const int j = w * spw + lane / L;              // slot within this CTA
     const int blk = (int)cl.block_rank();
-    const int p = blk * S + w;
+    const int p = blk * S + j;                     // slot within the cluster
+    const bool live = j < S && p < P;
     const int NR = 2 * P - 1;
     // [buf][slot][col][m] data, [buf][slot][col] norms, [buf][slot][col] indices
     double* data = rsm;
@@ -614,23 +920,13 @@ k_jacobi_ring(int m, int n, int P, double* __restrict__ W, int ldw, int* __restr
     auto D = [&](int buf, int slot, int col) { return data + (((size_t)buf * S + slot) * 2 + col) * m; };
     auto NI = [&](int buf, int slot, int col) { return ((buf * S + slot) * 2 + col); };
     const double tiny = tiny_rel * *frob2;
-    if (p < P) {
-        const int ia = p, ib = p == 0 ? NR : NR - p;
-        const int cols[2] = {ia, ib};
+    if (live) {
+        const int cols[2] = {p, p == 0 ? NR : NR - p};
         for (int c2 = 0; c2 < 2; ++c2) {
             const int ci = cols[c2];
-            double* d = D(0, w, c2);
-            double a = 0.0;
-            for (int i = lane; i < m; i += 32) {
-                const double x = ci < n ? W[(size_t)ci * ldw + i] : 0.0;
-                d[i] = x;
-                a = fma(x, x, a);
-            }
-            a = warp_sum(a);
-            if (lane == 0) {
-                nrm[NI(0, w, c2)] = a;
-                idx[NI(0, w, c2)] = ci;
-            }
+            double* d = D(0, j, c2);
+            for (int i = gl; i < m; i += L) d[i] = ci < n ? W[(size_t)ci * ldw + i] : 0.0;
+            if (gl == 0) idx[NI(0, j, c2)] = ci;
         }
     }
     cl.sync();
@@ -639,39 +935,80 @@ k_jacobi_ring(int m, int n, int P, double* __restrict__ W, int ldw, int* __restr
         int any = 0;
         for (int r = 0; r < NR; ++r) {
             const int nxt = cur ^ 1;
-            if (p < P) {
-                const double* da = D(cur, w, 0);
-                const double* db = D(cur, w, 1);
-                double al = nrm[NI(cur, w, 0)], be = nrm[NI(cur, w, 1)];
-                const int ia = idx[NI(cur, w, 0)], ib = idx[NI(cur, w, 1)];
-                double xa[KV], xb[KV];
+            double al = 0.0, be = 0.0;
+            int ia = n, ib = n;
+            double xa[KV], xb[KV];
+            if (live) {
+                const double* da = D(cur, j, 0);
+                const double* db = D(cur, j, 1);
+                al = nrm[NI(cur, j, 0)];
+                be = nrm[NI(cur, j, 1)];
+                ia = idx[NI(cur, j, 0)];
+                ib = idx[NI(cur, j, 1)];
 #pragma unroll
                 for (int k = 0; k < KV; ++k) {
-                    const int i = lane + 32 * k;
+                    const int i = gl + L * k;
                     xa[k] = i < m ? da[i] : 0.0;
                     xb[k] = i < m ? db[i] : 0.0;
                 }
-                if (ia < n && ib < n) {
-                    double ga = 0.0;
+            } else {
 #pragma unroll
-                    for (int k = 0; k < KV; ++k) ga = fma(xa[k], xb[k], ga);
-                    ga = warp_sum(ga);
-                    double cs, sn;
-                    if (jacobi_rotation(al, be, ga, tol, tiny, cs, sn)) {
-                        any = 1;
-                        double na = 0.0, nb = 0.0;
+                for (int k = 0; k < KV; ++k) xa[k] = xb[k] = 0.0;
+            }
+            if (r == 0) {
+                double na0 = 0.0, na1 = 0.0, nb0 = 0.0, nb1 = 0.0;
 #pragma unroll
-                        for (int k = 0; k < KV; ++k) {
-                            const double xn = cs * xa[k] - sn * xb[k], yn = sn * xa[k] + cs * xb[k];
-                            xa[k] = xn;
-                            xb[k] = yn;
-                            na = fma(xn, xn, na);
-                            nb = fma(yn, yn, nb);
-                        }
-                        al = warp_sum(na);
-                        be = warp_sum(nb);
+                for (int k = 0; k < KV; k += 2) {
+                    na0 = fma(xa[k], xa[k], na0);
+                    nb0 = fma(xb[k], xb[k], nb0);
+                    if (k + 1 < KV) {
+                        na1 = fma(xa[k + 1], xa[k + 1], na1);
+                        nb1 = fma(xb[k + 1], xb[k + 1], nb1);
                     }
                 }
+                al = group_sum(na0 + na1, L);
+                be = group_sum(nb0 + nb1, L);
+            }
+            double g0 = 0.0, g1 = 0.0;
+#pragma unroll
+            for (int k = 0; k < KV; k += 2) {
+                g0 = fma(xa[k], xb[k], g0);
+                if (k + 1 < KV) g1 = fma(xa[k + 1], xb[k + 1], g1);
+            }
+            const double ga = group_sum(g0 + g1, L);
+            double cs, sn, tg;
+            const bool rot = live && ia < n && ib < n && ring_rotation(al, be, ga, tol, tiny, cs, sn, tg);
+            if (rot) any = 1;
+            if (__any_sync(FULL, rot)) {
+                // groups that do not rotate carry cs = 1, sn = 0: their columns pass unchanged
+#pragma unroll
+                for (int k = 0; k < KV; ++k) {
+                    const double xn = cs * xa[k] - sn * xb[k], yn = sn * xa[k] + cs * xb[k];
+                    xa[k] = xn;
+                    xb[k] = yn;
+                }
+                double an = al - tg, bn = be + tg;
+                const bool refresh = rot && (an < 0.25 * al || bn < 0.25 * be);
+                if (__any_sync(FULL, refresh)) {
+                    double na = 0.0, nb = 0.0;
+#pragma unroll
+                    for (int k = 0; k < KV; ++k) {
+                        na = fma(xa[k], xa[k], na);
+                        nb = fma(xb[k], xb[k], nb);
+                    }
+                    na = group_sum(na, L);
+                    nb = group_sum(nb, L);
+                    if (refresh) {
+                        an = na;
+                        bn = nb;
+                    }
+                }
+                if (rot) {
+                    al = an;
+                    be = bn;
+                }
+            }
+            if (live) {
                 // destinations in the next round
                 int sa, ca, sb, cb;
                 if (p == 0) { sa = 1; ca = 1; sb = 0; cb = 1; }
@@ -681,13 +1018,13 @@ k_jacobi_ring(int m, int n, int P, double* __restrict__ W, int ldw, int* __restr
                 double* pb = cl.map_shared_rank(D(nxt, sb % S, cb), sb / S);
 #pragma unroll
                 for (int k = 0; k < KV; ++k) {
-                    const int i = lane + 32 * k;
+                    const int i = gl + L * k;
                     if (i < m) {
                         pa[i] = xa[k];
                         pb[i] = xb[k];
                     }
                 }
-                if (lane == 0) {
+                if (gl == 0) {
                     *cl.map_shared_rank(nrm + NI(nxt, sa % S, ca), sa / S) = al;
                     *cl.map_shared_rank(idx + NI(nxt, sa % S, ca), sa / S) = ia;
                     *cl.map_shared_rank(nrm + NI(nxt, sb % S, cb), sb / S) = be;
@@ -697,16 +1034,16 @@ k_jacobi_ring(int m, int n, int P, double* __restrict__ W, int ldw, int* __restr
             cl.sync();
             cur = nxt;
         }
-        if (any && lane == 0) flags[sw] = 1;
+        if (any && gl == 0) flags[sw] = 1;
         cl.sync();
         if (__ldcg(flags + sw) == 0) break;
     }
-    if (p < P) {
+    if (live) {
         for (int c2 = 0; c2 < 2; ++c2) {
-            const int ci = idx[NI(cur, w, c2)];
+            const int ci = idx[NI(cur, j, c2)];
             if (ci >= n) continue;
-            const double* d = D(cur, w, c2);
-            for (int i = lane; i < m; i += 32) W[(size_t)ci * ldw + i] = d[i];
+            const double* d = D(cur, j, c2);
+            for (int i = gl; i < m; i += L) W[(size_t)ci * ldw + i] = d[i];
         }
     }
     if (blk == 0 && threadIdx.x == 0) *sweeps_used = sw;
@@ -813,12 +1150,13 @@ __global__ void k_rank(int n, const double* __restrict__ nrm, int* __restrict__ 
 __global__ void k_permute_normalise(int m, int n, const double* __restrict__ W, int ldw,
                                     const double* __restrict__ nrm, const int* __restrict__ rank,
                                     double* __restrict__ sig, double* __restrict__ U,
-                                    const double* __restrict__ frob2) {
+                                    const double* __restrict__ frob2, const int* __restrict__ rowperm) {
     const int col = blockIdx.x;
     const int dst = rank[col];
     const double s = nrm[col];
     const double inv = (s > 0.0 && s * s > 1e-30 * *frob2) ? 1.0 / s : 0.0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) U[(size_t)dst * m + i] = W[(size_t)col * ldw + i] * inv;
+    for (int i = threadIdx.x; i < m; i += blockDim.x)
+        U[(size_t)dst * m + (rowperm ? rowperm[i] : i)] = W[(size_t)col * ldw + i] * inv;
     if (threadIdx.x == 0) sig[dst] = s;
 }
 }  // namespace
@@ -842,19 +1180,44 @@ static void jacobi_grid(tt_ctx* c, int m, int mr, int n, T* W, int ldw, T tol, d
         // flops; past about 1e5 entries a grid over more SMs (with its slower barrier)
         // finishes a round sooner
         if (mr == m && m <= 512 && P >= 2 && P <= 256 && (long long)m * n <= kJacobiRingMaxEntries) {
-            // one cluster, columns in distributed shared memory
-            auto kern = m <= 128 ? k_jacobi_ring<4> : m <= 256 ? k_jacobi_ring<8> : k_jacobi_ring<16>;
-            int G = 0, S = 0;
+            // one cluster, columns in distributed shared memory.  Pick the slot width L
+            // (lanes per pair) and entries per lane KV (L KV >= m) that minimise the FP64
+            // instructions an SM issues per round: warps per CTA x (dot KV + reduction
+            // log2 L + rotation ~40 + apply 4 KV), over clusters of 16 or 8 CTAs.
+            using RingKernel = void (*)(int, int, int, int, int, double*, int, int*, int, double, double,
+                                        const double*, int*);
+            const RingKernel kerns[3] = {k_jacobi_ring<8>, k_jacobi_ring<16>, k_jacobi_ring<32>};
+            const int kvs[3] = {8, 16, 32};
+            RingKernel kern = nullptr;
+            int G = 0, S = 0, L = 0, threads = 0;
             size_t smem = 0;
-            for (int g : {16, 8}) {
-                S = ceil_div(P, g);
-                if (S > 16) continue;
-                smem = (size_t)4 * S * m * sizeof(double) + (size_t)4 * S * (sizeof(double) + sizeof(int));
-                if (smem > 200 * 1024) continue;
-                CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-                if (max_cluster_ctas(c, (const void*)kern, 32 * S, smem) >= g) {
-                    G = ceil_div(P, S);
-                    break;
+            double best = 1e30;
+            for (int v = 0; v < 3; ++v) {
+                for (int l : {4, 8, 16, 32}) {
+                    if (l * kvs[v] < m) continue;
+                    int lg = 0;
+                    while ((1 << lg) < l) ++lg;
+                    for (int g : {16, 8}) {
+                        const int s = ceil_div(P, g);
+                        const int warps = ceil_div(s, 32 / l);
+                        if (warps > 8) continue;
+                        const size_t sm = (size_t)4 * s * m * sizeof(double) + (size_t)4 * s * (sizeof(double) + sizeof(int));
+                        if (sm > 200 * 1024) continue;
+                        const int gg = ceil_div(P, s);
+                        if (gg < 2) continue;
+                        const double cost = (double)warps * (5.0 * kvs[v] + lg + 40.0);
+                        if (cost >= best) continue;
+                        CUDA_CHECK(cudaFuncSetAttribute(kerns[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        227 * 1024));
+                        if (max_cluster_ctas(c, (const void*)kerns[v], 32 * warps, sm) < gg) continue;
+                        best = cost;
+                        kern = kerns[v];
+                        G = gg;
+                        S = s;
+                        L = l;
+                        threads = 32 * warps;
+                        smem = sm;
+                    }
                 }
             }
             if (G >= 2) {
@@ -863,7 +1226,7 @@ static void jacobi_grid(tt_ctx* c, int m, int mr, int n, T* W, int ldw, T tol, d
                 int* sweeps = flags.p + max_sweeps;
                 cudaLaunchConfig_t cfg = {};
                 cfg.gridDim = dim3(G);
-                cfg.blockDim = dim3(32 * S);
+                cfg.blockDim = dim3(threads);
                 cfg.dynamicSmemBytes = smem;
                 cfg.stream = c->stream;
                 cudaLaunchAttribute attr;
@@ -873,14 +1236,14 @@ static void jacobi_grid(tt_ctx* c, int m, int mr, int n, T* W, int ldw, T tol, d
                 attr.val.clusterDim.z = 1;
                 cfg.attrs = &attr;
                 cfg.numAttrs = 1;
-                CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, m, n, P, (double*)W, ldw, flags.p, max_sweeps, (double)tol,
-                                              tiny_rel, frob2, sweeps));
+                CUDA_CHECK(cudaLaunchKernelEx(&cfg, kern, m, n, P, L, S, (double*)W, ldw, flags.p, max_sweeps,
+                                              (double)tol, tiny_rel, frob2, sweeps));
                 count_launch(c);
                 static const bool log = getenv("TT_LOG_ROUND") != nullptr;
                 if (log) {
                     int h = 0;
                     read_back(c, (const int*)sweeps, &h, 1);
-                    fprintf(stderr, "jacobi%s-ring m=%d n=%d ctas=%d sweeps=%d\n", tag, m, n, G, h);
+                    fprintf(stderr, "jacobi%s-ring m=%d n=%d ctas=%d L=%d slots=%d sweeps=%d\n", tag, m, n, G, L, S, h);
                 }
                 return;
             }
@@ -949,8 +1312,10 @@ static void jacobi_grid(tt_ctx* c, int m, int mr, int n, T* W, int ldw, T tol, d
     }
 }
 
-static void jacobi_columns(tt_ctx* c, int m, int n, double* W, double* sig, double* U, double ortho_tol) {
-    // W: m x n column-major (ld m), overwritten by W V (orthogonal columns)
+static void jacobi_columns(tt_ctx* c, int m, int n, double* W, double* sig, double* U, double ortho_tol,
+                           const int* rowperm) {
+    // W: m x n column-major (ld m), overwritten by W V (orthogonal columns); row i of W
+    // is row rowperm[i] of U (identity when null)
     const int max_sweeps = 60;
     // Orthogonality target: FP64 dot products of nearly orthogonal columns carry
     // rounding noise of order m eps_mach, so a tighter target only re-rotates noise.
@@ -973,25 +1338,27 @@ static void jacobi_columns(tt_ctx* c, int m, int n, double* W, double* sig, doub
     LAUNCH_CHECK(c);
     k_rank<<<ceil_div(n, 256), 256, 0, c->stream>>>(n, nrm.p, rank.p);
     LAUNCH_CHECK(c);
-    k_permute_normalise<<<n, 256, 0, c->stream>>>(m, n, W, m, nrm.p, rank.p, sig, U, frob2.p);
+    k_permute_normalise<<<n, 256, 0, c->stream>>>(m, n, W, m, nrm.p, rank.p, sig, U, frob2.p, rowperm);
     LAUNCH_CHECK(c);
 }
 
 void left_svd(tt_ctx* c, int m, int n, MatView A, double* sig, double* U, double ortho_tol) {
     TT_REQUIRE(m > 0 && n > 0, "left_svd: empty matrix");
-    // The SVD is FP64 on both precision paths.  A^T = Q R (Householder, R is k x m
-    // with k = min(m, n)) gives A = R^T Q^T: the left singular vectors of A are those
-    // of the m x k matrix R^T, and one-sided Jacobi on R^T converges in far fewer
-    // sweeps than on A itself (the triangular factor is already close to orthogonal
-    // columns; cf. QR-preconditioned Jacobi, Drmac and Veselic 2008).
+    // The SVD is FP64 on both precision paths.  A^T P = Q R (Householder with column
+    // pivoting, R is k x m with k = min(m, n)) gives P^T A = R^T Q^T: the left singular
+    // vectors of A are those of the m x k matrix R^T with rows permuted by P, and
+    // one-sided Jacobi on R^T converges in far fewer sweeps than on A itself (the
+    // triangular factor of a pivoted QR has nearly orthogonal, graded columns;
+    // QR-preconditioned Jacobi, Drmac and Veselic 2008).
     PrecScope fp64(c, 0);
     const int k = std::min(m, n);
     DBuf<double> R(c, (size_t)k * m);
-    qr_r(c, n, m, trans(A), R.p, m);        // R: k x m row-major
+    DBuf<int> perm(c, m);
+    const bool pivoted = qr_r_launch<double>(c, n, m, trans(A), R.p, m, perm.p);   // R: k x m row-major
     // W = R^T column-major (m x k): W(i, j) = R(j, i) at j*m + i = R[j*m + i]
     DBuf<double> W(c, (size_t)m * k);
     CUDA_CHECK(cudaMemcpyAsync(W.p, R.p, (size_t)m * k * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    jacobi_columns(c, m, k, W.p, sig, U, ortho_tol);
+    jacobi_columns(c, m, k, W.p, sig, U, ortho_tol, pivoted ? perm.p : nullptr);
 }
 
 // ============================================================== truncation

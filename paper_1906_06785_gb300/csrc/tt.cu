@@ -161,6 +161,14 @@ __global__ void k_scale_cols(int m, double* __restrict__ X, int ld, const double
     const double f = mode == 0 ? sqrt(fabs(v)) : mode == 1 ? (v > 0.0 ? 1.0 / v : 0.0) : v;
     for (int i = threadIdx.x; i < m; i += blockDim.x) X[(size_t)j * ld + i] *= f;
 }
+
+// H = (3 I - G) / 2 in place (n x n, column-major): the Newton-Schulz step for the
+// polar factor, U <- U H with G = U^T U
+__global__ void k_ns_shift(int n, double* __restrict__ G) {
+    const long long len = (long long)n * n;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len; t += (long long)gridDim.x * blockDim.x)
+        G[t] = (t % n == t / n ? 1.5 : 0.0) - 0.5 * G[t];
+}
 }  // namespace
 
 // Truncation through Gram matrices, for tolerances well above sqrt(machine eps):
@@ -262,6 +270,19 @@ static TTPtr round_gram(tt_ctx* c, const tt_t* z, double eps, RoundOut* info, in
         gemm(c, m, r2, R2, 1.0, rowmaj(Bm.p, R2), colmaj(V.p, R2), 0.0, colmaj(U2.p, m));
         k_scale_cols<<<r2, 128, 0, c->stream>>>(m, U2.p, m, sig2.p, 1);
         LAUNCH_CHECK(c);
+        // U2 = B V Sigma^-1 carries V's angular error (the Jacobi tolerance) amplified by
+        // sigma_max / sigma_i: its span is right to that tolerance, the orthogonality of
+        // its columns is not.  Two Newton-Schulz steps U2 <- U2 (3 I - U2^T U2) / 2 take
+        // it to the nearest orthonormal frame (the polar factor), same span.
+        DBuf<double> G(c, (size_t)r2 * r2), U2n(c, (size_t)m * r2);
+        for (int it = 0; it < 2; ++it) {
+            gemm(c, r2, r2, m, 1.0, trans(colmaj(U2.p, m)), colmaj(U2.p, m), 0.0, colmaj(G.p, r2));
+            k_ns_shift<<<ceil_div(r2 * r2, 256), 256, 0, c->stream>>>(r2, G.p);
+            LAUNCH_CHECK(c);
+            gemm(c, m, r2, r2, 1.0, colmaj(U2.p, m), colmaj(G.p, r2), 0.0, colmaj(U2n.p, m));
+            CUDA_CHECK(cudaMemcpyAsync(U2.p, U2n.p, (size_t)m * r2 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                       c->stream));
+        }
     }
     TTPtr out = wrap(tt_alloc(c, n_t, n_xi, n_x, r1, r2));
     CUDA_CHECK(cudaMemcpyAsync(out->z1, U1.p, (size_t)n_t * r1 * sizeof(double), cudaMemcpyDeviceToDevice,

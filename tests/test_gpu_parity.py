@@ -83,6 +83,8 @@ def test_dot_and_axpby(ctx, shape):
     ((20, 6, 1312, 20, 60), 1e-6),   # several row blocks, ragged tail
     ((100, 20, 5440, 30, 90), 1e-5), # medium-sized velocity train
     ((11, 3, 40, 9, 120), 1e-8),     # wide: n_x < pre-rounding rank
+    ((40, 6, 1500, 40, 240), 1e-6),  # first rank above n_t; 150-column SVDs
+    ((24, 20, 1200, 24, 300), 1e-6), # 320 x 301 SVD: 16 lanes x 32 entries per pair
 ])
 def test_round_matches_oracle(ctx, shape, eps):
     n_t, n_xi, n_x, r1, r2 = shape

@@ -21,12 +21,12 @@ def ctx():
     return binding.Context()
 
 
-def _wide_sum(n_t, n_xi, n_x, parts, r1, r2, seed):
+def _wide_sum(n_t, n_xi, n_x, parts, r1, r2, seed, decay=16):
     """A sum of `parts` trains with graded spectra: second rank parts * r2 (like a Krylov
     sum or a matvec output), numerical rank far lower."""
     z = None
     for k in range(parts):
-        t = otm.TT(*synth.random_tt(n_t, n_xi, n_x, r1, r2, seed=seed + k, decay=8))
+        t = otm.TT(*synth.random_tt(n_t, n_xi, n_x, r1, r2, seed=seed + k, decay=decay))
         z = t if z is None else otm.add((1.0, z), (0.5 ** k, t))
     return z
 
@@ -53,7 +53,7 @@ def test_randomized_truncation_meets_the_bound(ctx, eps):
 
 
 def test_small_second_rank_takes_the_deterministic_route(ctx):
-    z = otm.TT(*synth.random_tt(10, 5, 300, 6, 40, seed=62, decay=6))
+    z = otm.TT(*synth.random_tt(10, 8, 300, 6, 40, seed=62, decay=6))
     t = ctx.tt(z.z1, z.z2, z.z3)
     g, nb, na, ell = ctx.round_randomized(t, 1e-4, seed=3)
     d, nb2, na2 = ctx.round(t, 1e-4)
