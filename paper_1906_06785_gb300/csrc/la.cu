@@ -976,7 +976,9 @@ k_jacobi_ring(int m, int n, int P, int L, int S, double* __restrict__ W, int ldw
                 if (k + 1 < KV) g1 = fma(xa[k + 1], xb[k + 1], g1);
             }
             const double ga = group_sum(g0 + g1, L);
-            double cs, sn, tg;
+            // a slot that does not rotate (dummy column, no live slot, or orthogonal
+            // already) applies the identity when another group of its warp rotates
+            double cs = 1.0, sn = 0.0, tg = 0.0;
             const bool rot = live && ia < n && ib < n && ring_rotation(al, be, ga, tol, tiny, cs, sn, tg);
             if (rot) any = 1;
             if (__any_sync(FULL, rot)) {

@@ -230,16 +230,15 @@ static TTPtr round_gram(tt_ctx* c, const tt_t* z, double eps, RoundOut* info, in
     // 2 R2^3 < m^3, B^T B (R2 x R2) with B = C2_left F and G3 = F F^T (F = eigenvectors
     // of G3 scaled by the square roots of its eigenvalues): Y Y^T = B B^T, so the
     // eigenpairs (V, Sigma^2) of B^T B give the left singular vectors U2 = B V Sigma^-1.
-    const bool rside = !wide && R2 < n_x && 2.0 * R2 * R2 * (double)R2 < (double)m * m * m;
+    const bool rside = !wide && 2.0 * R2 * R2 * (double)R2 < (double)m * m * m;
     const int p2 = rside ? R2 : m;
     DBuf<double> sig2(c, p2), U2(c, (size_t)m * p2), Bm, V;
     if (rside) {
-        // F = V_z Sigma_z from the SVD of z3^T (QR-preconditioned Jacobi on the factor, so
-        // the only squaring of a spectrum is the one of B^T B below)
-        // (the narrow route has R2 < n_x, so z3^T has R2 singular values)
+        // F from the eigenpairs of G3 (already at hand): the same squared spectrum as
+        // S2's, with no QR of the n_x-row core
         DBuf<double> lg(c, R2), Ug(c, (size_t)R2 * R2);
-        left_svd(c, R2, n_x, trans(rowmaj(z->z3, R2)), lg.p, Ug.p);
-        k_scale_cols<<<R2, 128, 0, c->stream>>>(R2, Ug.p, R2, lg.p, 2);
+        left_svd(c, R2, R2, colmaj(G3.p, R2), lg.p, Ug.p);
+        k_scale_cols<<<R2, 128, 0, c->stream>>>(R2, Ug.p, R2, lg.p, 0);
         LAUNCH_CHECK(c);
         Bm.alloc(c, (size_t)m * R2);
         gemm(c, m, R2, R2, 1.0, rowmaj(C2.p, R2), colmaj(Ug.p, R2), 0.0, rowmaj(Bm.p, R2));
