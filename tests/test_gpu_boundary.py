@@ -148,11 +148,12 @@ def test_picard_resumes_from_a_given_iterate(ctx, binding):
 
 
 def test_device_wait_limit_gives_timeout_and_recovers(ctx, binding):
-    """A cooperative Householder R factor over many CTAs (n_x = 6000 rows of z3
-    spread over the whole GPU) with a wait limit of 0 polls: blocks that reach a grid
-    barrier before the others give up, the call returns TT_ETIMEOUT, and with the
-    default limit the same call succeeds on the same context."""
-    z = otm.TT(*synth.random_tt(6, 3, 6000, 4, 12, seed=41, decay=4))
+    """A cooperative Householder R factor over many CTAs (n_x = 60000 rows of z3, more
+    than one cluster's shared memory holds, spread over the whole GPU) with a wait limit
+    of 0 polls: blocks that reach a grid barrier before the others give up, the call
+    returns TT_ETIMEOUT, and with the default limit the same call succeeds on the same
+    context."""
+    z = otm.TT(*synth.random_tt(6, 3, 60000, 4, 12, seed=41, decay=4))
     t = ctx.tt(z.z1, z.z2, z.z3)
     ref, nref = otm.round_tt(z, 1e-8)
     ctx.set_wait_limit(0)
