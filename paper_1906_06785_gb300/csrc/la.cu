@@ -193,6 +193,7 @@ struct QRParams {
     unsigned* bar;
     int* status;
     const double* fnorm;   // ||A||_F^2 (FP32 arithmetic works on A / ||A||_F), or null
+    const double* fro2;    // ||A||_F^2 (zero-column threshold)
     long long wait_limit;  // grid-barrier polls before DEV_TIMEOUT
 };
 
@@ -262,6 +263,9 @@ __global__ void __launch_bounds__(256) k_qr_r(QRParams<TC> P) {
         sc = (f > 0.0 && f < 1e300) ? f : 1.0;
     }
     const double inv = 1.0 / sc;
+    // numerically zero column: remaining squared norm at most 1e-30 ||A||_F^2 (in the
+    // scaled units of the working copy)
+    const TC thr = TC(1e-30 * __ldcg(P.fro2) * inv * inv);
     for (int l = warp; l < P.c; l += nw)
         for (int i = lane; i < rows; i += 32)
             W[(size_t)l * P.nbp + i] = TC(P.A[(long long)(row0 + i) * P.rs + (long long)l * P.cs] * inv);
@@ -284,10 +288,10 @@ __global__ void __launch_bounds__(256) k_qr_r(QRParams<TC> P) {
         const TC ss = __ldcg(P.sums), x0 = __ldcg(P.sums + 1 + P.c + j);
         const int jloc = j - row0;
         const bool own = jloc >= 0 && jloc < rows;
-        // zero column (FP32: below 1e-15 of the unit-norm input, where 1 / (v^T v)
-        // would overflow): R(j, :) is row j as it stands
-        const TC zero_ss = sizeof(TC) < sizeof(double) ? TC(1e-30) : TC(0);
-        if (ss <= zero_ss) {
+        // numerically zero column (Householder steps on it would only shrink rounding
+        // noise towards the underflow range, where 2 / v^T v overflows): R(j, :) is row j
+        // as it stands
+        if (ss <= thr) {
             if (own)
                 for (int l = tid; l < P.c; l += blockDim.x)
                     P.R[(size_t)j * P.ldr + l] = l < j ? 0.0 : (double)W[(size_t)l * P.nbp + jloc] * sc;
@@ -380,9 +384,11 @@ __global__ void __launch_bounds__(256) k_qr_cl(QRClParams<TC> P) {
         }
     }
     __syncthreads();
-    if (pivot) {
-        // column norms over all rows: partials in buffer 1 (column 0 writes buffer 0, and
-        // no CTA writes buffer 1 before every CTA has passed column 0's barrier)
+    // column norms over all rows (pivot order) and ||A||_F^2 (zero-column threshold):
+    // partials in buffer 1 (column 0 writes buffer 0, and no CTA writes buffer 1 before
+    // every CTA has passed column 0's barrier)
+    TC thr;
+    {
         TC* np = part + L;
         for (int l = tid; l < c; l += nt) {
             const TC* w2 = W + (size_t)l * P.nbp;
@@ -392,11 +398,22 @@ __global__ void __launch_bounds__(256) k_qr_cl(QRClParams<TC> P) {
             pidx[l] = l;
         }
         cl.sync();
+        TC f = TC(0);
         for (int l = tid; l < c; l += nt) {
             TC s = TC(0);
             for (int q = 0; q < G; ++q) s += *cl.map_shared_rank(np + l, q);
             nrm2[l] = s;
+            f += s;
         }
+        f = warp_sum(f);
+        if (lane == 0) red[warp] = f;
+        __syncthreads();
+        f = TC(0);
+        for (int q = 0; q < (nt >> 5); ++q) f += red[q];
+        // a column whose remaining squared norm is at most 1e-30 ||A||_F^2 is numerically
+        // zero: Householder steps on such columns only shrink rounding noise further,
+        // towards the underflow range where 2 / v^T v overflows
+        thr = TC(1e-30) * f;
         __syncthreads();
     }
     for (int j = 0; j < P.k; ++j) {
@@ -497,10 +514,8 @@ __global__ void __launch_bounds__(256) k_qr_cl(QRClParams<TC> P) {
         }
         __syncthreads();
         const TC ss = sums[0], x0 = sums[1 + c + j];
-        // zero column (FP32: below 1e-15 of the unit-norm input, where 1 / (v^T v)
-        // would overflow): row j stays as it stands
-        const TC zero_ss = sizeof(TC) < sizeof(double) ? TC(1e-30) : TC(0);
-        if (ss <= zero_ss) continue;
+        // numerically zero column: row j stays as it stands
+        if (ss <= thr) continue;
         const TC sigma = sqrt(ss);
         const TC alpha = x0 >= TC(0) ? -sigma : sigma;
         const TC v0 = x0 - alpha;
@@ -635,6 +650,17 @@ bool qr_r_launch(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr, int*
         gwork.alloc(c, (size_t)G * nbp * cols);
     }
     DBuf<TC> scratch(c, (size_t)G * L + L);
+    DBuf<double> f2;
+    const double* fro2 = fn.p;
+    if (!fro2) {
+        f2.alloc(c, 1);
+        CUDA_CHECK(cudaMemsetAsync(f2.p, 0, sizeof(double), c->stream));
+        const long long len = (long long)n * cols;
+        const int fb = (int)std::min<long long>(2LL * c->nsm, std::max(1LL, (len + 255) / 256));
+        k_frob2_strided<<<fb, 256, 0, c->stream>>>(n, cols, A.p, A.s0, A.s1, f2.p);
+        LAUNCH_CHECK(c);
+        fro2 = f2.p;
+    }
     QRParams<TC> P;
     P.n = n; P.c = cols; P.k = k; P.nb = nb; P.nbp = nbp; P.L = L;
     P.A = A.p; P.rs = A.s0; P.cs = A.s1;
@@ -645,6 +671,7 @@ bool qr_r_launch(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr, int*
     P.bar = c->dbarrier;
     P.status = c->dstatus;
     P.fnorm = fn.p;
+    P.fro2 = fro2;
     P.wait_limit = c->wait_limit;
     CUDA_CHECK(cudaMemsetAsync(c->dbarrier, 0, 2 * sizeof(unsigned), c->stream));
     CUDA_CHECK(cudaFuncSetAttribute(k_qr_r<TC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
@@ -853,13 +880,16 @@ __device__ __forceinline__ double group_sum(double v, int L) {
     return v;
 }
 
-// The rotation of jacobi_rotation written with two reciprocal square roots and no
-// division: with q = (be - al)^2 + (2 ga)^2, cos 2theta = |be - al| / sqrt(q) and
-// sin 2theta = sign(be - al) 2 ga / sqrt(q); h = (1 + cos 2theta) / 2 gives
-// cs = sqrt(h) = h / sqrt(h), sn = sin 2theta / (2 cs) and t = tan theta = sn / cs.
-// The same inner rotation (|theta| <= pi/4) as t = sign(zeta) / (|zeta| + sqrt(1 +
-// zeta^2)); every lane of a group computes it from group-uniform al, be, ga.
-// tg = t ga is the squared norm the rotation moves from column a to column b.
+// The rotation of jacobi_rotation with its angle taken in FP32 and its cosine in FP64.
+// Only the transformation has to be orthogonal to FP64 precision, not the angle exact:
+// t = tan theta = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (be - al) / (2 ga), is
+// evaluated in FP32 on be - al and 2 ga scaled by the same power of two (exact), then
+// cs = 1 / sqrt(1 + t^2) and sn = cs t in FP64 from that t, so cs^2 + sn^2 = 1 to FP64
+// rounding and the rotation changes no singular value.  An angle off by FP32 rounding
+// leaves |ga| at ~1e-7 of its value, which the next sweep removes.  The FP64
+// dependency chain of a round shrinks from the ~35 operations of two FP64 square roots
+// and a division to ~12.  Every lane of a group computes it from group-uniform al, be,
+// ga; tg = t ga is the squared norm the rotation moves from column a to column b.
 __device__ __forceinline__ bool ring_rotation(double al, double be, double ga, double tol, double tiny,
                                               double& cs, double& sn, double& tg) {
     const bool rot = al > tiny && be > tiny && ga * ga > (tol * tol * al) * be;
@@ -868,14 +898,18 @@ __device__ __forceinline__ bool ring_rotation(double al, double be, double ga, d
     tg = 0.0;
     if (rot) {
         const double d = be - al, g2 = 2.0 * ga;
-        const double ir = rsqrt(fma(d, d, g2 * g2));
-        const double c2 = fabs(d) * ir;
-        const double s2 = copysign(1.0, d) * g2 * ir;
-        const double h = fma(0.5, c2, 0.5);
-        const double rh = rsqrt(h);
-        cs = h * rh;
-        sn = 0.5 * s2 * rh;
-        tg = (sn * rh) * ga;
+        // power of two 2^-e with max(|d|, |g2|) 2^-e in [1, 2): both fit FP32 (|g2| >= 1e-28
+        // |d| here, since columns below tiny are not rotated)
+        const int hi = max(__double2hiint(fabs(d)), __double2hiint(fabs(g2)));
+        const int e = ((hi >> 20) & 0x7ff) - 1023;
+        const double sc = __hiloint2double((1023 - e) << 20, 0);
+        const float z = (float)(d * sc) / (float)(g2 * sc);
+        const float az = fabsf(z);
+        const float r = az > 1e18f ? az : sqrtf(fmaf(az, az, 1.0f));
+        const double t = (double)copysignf(1.0f / (az + r), z);
+        cs = rsqrt(fma(t, t, 1.0));
+        sn = cs * t;
+        tg = t * ga;
     }
     return rot;
 }
@@ -969,13 +1003,10 @@ k_jacobi_ring(int m, int n, int P, int L, int S, double* __restrict__ W, int ldw
                 al = group_sum(na0 + na1, L);
                 be = group_sum(nb0 + nb1, L);
             }
-            double g0 = 0.0, g1 = 0.0;
+            double g[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-            for (int k = 0; k < KV; k += 2) {
-                g0 = fma(xa[k], xb[k], g0);
-                if (k + 1 < KV) g1 = fma(xa[k + 1], xb[k + 1], g1);
-            }
-            const double ga = group_sum(g0 + g1, L);
+            for (int k = 0; k < KV; ++k) g[k & 3] = fma(xa[k], xb[k], g[k & 3]);
+            const double ga = group_sum((g[0] + g[1]) + (g[2] + g[3]), L);
             // a slot that does not rotate (dummy column, no live slot, or orthogonal
             // already) applies the identity when another group of its warp rotates
             double cs = 1.0, sn = 0.0, tg = 0.0;
