@@ -504,9 +504,15 @@ __global__ void __launch_bounds__(256) k_qr_cl(QRClParams<TC> P) {
         for (int t = tid; t < 1 + nl + (c - j); t += nt) {
             if (t <= nl) {
                 const int idx = t == 0 ? 0 : 1 + j + t;
-                TC s = TC(0);
-                for (int q = 0; q < G; ++q) s += *cl.map_shared_rank(part + (j & 1) * L + idx, q);
-                sums[idx] = s;
+                // all G remote loads in flight at once, then a fixed-order sum
+                TC v[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) v[q] = q < G ? *cl.map_shared_rank(part + (j & 1) * L + idx, q) : TC(0);
+#pragma unroll
+                for (int w2 = 8; w2 > 0; w2 >>= 1)
+#pragma unroll
+                    for (int q = 0; q < w2; ++q) v[q] += v[q + w2];
+                sums[idx] = v[0];
             } else {
                 const int idx = 1 + c + j + (t - 1 - nl);
                 sums[idx] = *cl.map_shared_rank(part + (j & 1) * L + idx, owner);
