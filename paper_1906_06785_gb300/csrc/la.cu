@@ -960,7 +960,35 @@ k_jacobi_ring(int m, int n, int P, int L, int S, double* __restrict__ W, int ldw
     auto D = [&](int buf, int slot, int col) { return data + (((size_t)buf * S + slot) * 2 + col) * m; };
     auto NI = [&](int buf, int slot, int col) { return ((buf * S + slot) * 2 + col); };
     const double tiny = tiny_rel * *frob2;
+    // this slot's columns in both buffers, and where they go in the next round (fixed
+    // for the whole kernel: the ring shift does not depend on the round), resolved once
+    // (scalars, not arrays, so that they stay in registers)
+    const double *la0 = nullptr, *la1 = nullptr, *lb0 = nullptr, *lb1 = nullptr;
+    double *ra0 = nullptr, *ra1 = nullptr, *rb0 = nullptr, *rb1 = nullptr;
+    double *rna0 = nullptr, *rna1 = nullptr, *rnb0 = nullptr, *rnb1 = nullptr;
+    int *ria0 = nullptr, *ria1 = nullptr, *rib0 = nullptr, *rib1 = nullptr;
+    int lna = 0, lnb = 0;
     if (live) {
+        int sa, ca, sb, cb;
+        if (p == 0) { sa = 1; ca = 1; sb = 0; cb = 1; }
+        else if (p == P - 1) { sa = p - 1; ca = 0; sb = p; cb = 0; }
+        else { sa = p - 1; ca = 0; sb = p + 1; cb = 1; }
+        la0 = D(0, j, 0); la1 = D(1, j, 0);
+        lb0 = D(0, j, 1); lb1 = D(1, j, 1);
+        ra0 = cl.map_shared_rank(D(0, sa % S, ca), sa / S);
+        ra1 = cl.map_shared_rank(D(1, sa % S, ca), sa / S);
+        rb0 = cl.map_shared_rank(D(0, sb % S, cb), sb / S);
+        rb1 = cl.map_shared_rank(D(1, sb % S, cb), sb / S);
+        rna0 = cl.map_shared_rank(nrm + NI(0, sa % S, ca), sa / S);
+        rna1 = cl.map_shared_rank(nrm + NI(1, sa % S, ca), sa / S);
+        rnb0 = cl.map_shared_rank(nrm + NI(0, sb % S, cb), sb / S);
+        rnb1 = cl.map_shared_rank(nrm + NI(1, sb % S, cb), sb / S);
+        ria0 = cl.map_shared_rank(idx + NI(0, sa % S, ca), sa / S);
+        ria1 = cl.map_shared_rank(idx + NI(1, sa % S, ca), sa / S);
+        rib0 = cl.map_shared_rank(idx + NI(0, sb % S, cb), sb / S);
+        rib1 = cl.map_shared_rank(idx + NI(1, sb % S, cb), sb / S);
+        lna = NI(0, j, 0);
+        lnb = NI(0, j, 1);
         const int cols[2] = {p, p == 0 ? NR : NR - p};
         for (int c2 = 0; c2 < 2; ++c2) {
             const int ci = cols[c2];
@@ -969,6 +997,7 @@ k_jacobi_ring(int m, int n, int P, int L, int S, double* __restrict__ W, int ldw
             if (gl == 0) idx[NI(0, j, c2)] = ci;
         }
     }
+    const int bstride = 2 * S;                     // norm/index entries per buffer
     cl.sync();
     int cur = 0, sw = 0;
     for (; sw < max_sweeps; ++sw) {
@@ -979,12 +1008,12 @@ k_jacobi_ring(int m, int n, int P, int L, int S, double* __restrict__ W, int ldw
             int ia = n, ib = n;
             double xa[KV], xb[KV];
             if (live) {
-                const double* da = D(cur, j, 0);
-                const double* db = D(cur, j, 1);
-                al = nrm[NI(cur, j, 0)];
-                be = nrm[NI(cur, j, 1)];
-                ia = idx[NI(cur, j, 0)];
-                ib = idx[NI(cur, j, 1)];
+                const double* da = cur ? la1 : la0;
+                const double* db = cur ? lb1 : lb0;
+                al = nrm[lna + cur * bstride];
+                be = nrm[lnb + cur * bstride];
+                ia = idx[lna + cur * bstride];
+                ib = idx[lnb + cur * bstride];
 #pragma unroll
                 for (int k = 0; k < KV; ++k) {
                     const int i = gl + L * k;
@@ -996,18 +1025,14 @@ k_jacobi_ring(int m, int n, int P, int L, int S, double* __restrict__ W, int ldw
                 for (int k = 0; k < KV; ++k) xa[k] = xb[k] = 0.0;
             }
             if (r == 0) {
-                double na0 = 0.0, na1 = 0.0, nb0 = 0.0, nb1 = 0.0;
+                double na[2] = {0.0, 0.0}, nb[2] = {0.0, 0.0};
 #pragma unroll
-                for (int k = 0; k < KV; k += 2) {
-                    na0 = fma(xa[k], xa[k], na0);
-                    nb0 = fma(xb[k], xb[k], nb0);
-                    if (k + 1 < KV) {
-                        na1 = fma(xa[k + 1], xa[k + 1], na1);
-                        nb1 = fma(xb[k + 1], xb[k + 1], nb1);
-                    }
+                for (int k = 0; k < KV; ++k) {
+                    na[k & 1] = fma(xa[k], xa[k], na[k & 1]);
+                    nb[k & 1] = fma(xb[k], xb[k], nb[k & 1]);
                 }
-                al = group_sum(na0 + na1, L);
-                be = group_sum(nb0 + nb1, L);
+                al = group_sum(na[0] + na[1], L);
+                be = group_sum(nb[0] + nb[1], L);
             }
             double g[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
@@ -1019,7 +1044,6 @@ k_jacobi_ring(int m, int n, int P, int L, int S, double* __restrict__ W, int ldw
             const bool rot = live && ia < n && ib < n && ring_rotation(al, be, ga, tol, tiny, cs, sn, tg);
             if (rot) any = 1;
             if (__any_sync(FULL, rot)) {
-                // groups that do not rotate carry cs = 1, sn = 0: their columns pass unchanged
 #pragma unroll
                 for (int k = 0; k < KV; ++k) {
                     const double xn = cs * xa[k] - sn * xb[k], yn = sn * xa[k] + cs * xb[k];
@@ -1048,13 +1072,8 @@ k_jacobi_ring(int m, int n, int P, int L, int S, double* __restrict__ W, int ldw
                 }
             }
             if (live) {
-                // destinations in the next round
-                int sa, ca, sb, cb;
-                if (p == 0) { sa = 1; ca = 1; sb = 0; cb = 1; }
-                else if (p == P - 1) { sa = p - 1; ca = 0; sb = p; cb = 0; }
-                else { sa = p - 1; ca = 0; sb = p + 1; cb = 1; }
-                double* pa = cl.map_shared_rank(D(nxt, sa % S, ca), sa / S);
-                double* pb = cl.map_shared_rank(D(nxt, sb % S, cb), sb / S);
+                double* pa = nxt ? ra1 : ra0;
+                double* pb = nxt ? rb1 : rb0;
 #pragma unroll
                 for (int k = 0; k < KV; ++k) {
                     const int i = gl + L * k;
@@ -1064,10 +1083,10 @@ k_jacobi_ring(int m, int n, int P, int L, int S, double* __restrict__ W, int ldw
                     }
                 }
                 if (gl == 0) {
-                    *cl.map_shared_rank(nrm + NI(nxt, sa % S, ca), sa / S) = al;
-                    *cl.map_shared_rank(idx + NI(nxt, sa % S, ca), sa / S) = ia;
-                    *cl.map_shared_rank(nrm + NI(nxt, sb % S, cb), sb / S) = be;
-                    *cl.map_shared_rank(idx + NI(nxt, sb % S, cb), sb / S) = ib;
+                    *(nxt ? rna1 : rna0) = al;
+                    *(nxt ? ria1 : ria0) = ia;
+                    *(nxt ? rnb1 : rnb0) = be;
+                    *(nxt ? rib1 : rib0) = ib;
                 }
             }
             cl.sync();
@@ -1220,20 +1239,24 @@ static void jacobi_grid(tt_ctx* c, int m, int mr, int n, T* W, int ldw, T tol, d
         // finishes a round sooner
         if (mr == m && m <= 512 && P >= 2 && P <= 256 && (long long)m * n <= kJacobiRingMaxEntries) {
             // one cluster, columns in distributed shared memory.  Pick the slot width L
-            // (lanes per pair) and entries per lane KV (L KV >= m) that minimise the FP64
-            // instructions an SM issues per round: warps per CTA x (dot KV + reduction
-            // log2 L + rotation ~40 + apply 4 KV), over clusters of 16 or 8 CTAs.
+            // (lanes per pair) and entries per lane KV (L KV >= m) for the shortest round:
+            // a round is bound either by one warp's instruction stream (~200 + 45 KV + 8
+            // log2 L dependent instructions at ~8 cycles each: ncu shows "wait" stalls
+            // dominating a one-warp-per-SM ring) or by the SM's FP64 pipe (warps per CTA x
+            // (5 KV + log2 L + 12) FP64 instructions at 16 cycles each), over clusters of 16
+            // or 8 CTAs.
             using RingKernel = void (*)(int, int, int, int, int, double*, int, int*, int, double, double,
                                         const double*, int*);
-            const RingKernel kerns[3] = {k_jacobi_ring<8>, k_jacobi_ring<16>, k_jacobi_ring<32>};
-            const int kvs[3] = {8, 16, 32};
+            const RingKernel kerns[5] = {k_jacobi_ring<2>, k_jacobi_ring<4>, k_jacobi_ring<8>, k_jacobi_ring<16>,
+                                         k_jacobi_ring<32>};
+            const int kvs[5] = {2, 4, 8, 16, 32};
             RingKernel kern = nullptr;
             int G = 0, S = 0, L = 0, threads = 0;
             size_t smem = 0;
             double best = 1e30;
-            for (int v = 0; v < 3; ++v) {
+            for (int v = 0; v < 5; ++v) {
                 for (int l : {4, 8, 16, 32}) {
-                    if (l * kvs[v] < m) continue;
+                    if (l * kvs[v] < m || (kvs[v] > 2 && l * kvs[v] >= 2 * m)) continue;
                     int lg = 0;
                     while ((1 << lg) < l) ++lg;
                     for (int g : {16, 8}) {
@@ -1244,7 +1267,9 @@ static void jacobi_grid(tt_ctx* c, int m, int mr, int n, T* W, int ldw, T tol, d
                         if (sm > 200 * 1024) continue;
                         const int gg = ceil_div(P, s);
                         if (gg < 2) continue;
-                        const double cost = (double)warps * (5.0 * kvs[v] + lg + 40.0);
+                        const double chain = 8.0 * (200.0 + 45.0 * kvs[v] + 8.0 * lg);
+                        const double pipe = 16.0 * warps * (5.0 * kvs[v] + lg + 12.0);
+                        const double cost = std::max(chain, pipe);
                         if (cost >= best) continue;
                         CUDA_CHECK(cudaFuncSetAttribute(kerns[v], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                         227 * 1024));
