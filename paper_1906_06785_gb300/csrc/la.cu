@@ -602,9 +602,10 @@ bool qr_r_launch(tt_ctx* c, int n, int cols, MatView A, double* R, int ldr, int*
     ProfScope prof(c, PROF_QR, 2.0 * kk * kk * ((double)n + cols - kk) - 2.0 * kk * kk * kk / 3.0,
                    8.0 * ((double)n * cols + kk * cols));
     {
-        // one cluster of up to 16 CTAs with the rows in shared memory (at least 16 rows
-        // a CTA): one cluster barrier per column
-        const int Gc = std::min(16, std::max(1, ceil_div(n, 16)));
+        // one cluster of up to 16 CTAs with the rows in shared memory (at least 4 rows a
+        // CTA: the FP64 work of a column spreads over as many SMs as the cluster has, at
+        // one cluster barrier per column)
+        const int Gc = std::min(16, std::max(1, ceil_div(n, 4)));
         const int nbc = ceil_div(n, Gc);
         const int Gu = ceil_div(n, nbc);
         const int nbpc = nbc | 1;
