@@ -136,3 +136,57 @@ def pressure_mass(mesh):
         R.append(np.repeat(pn, 4)); C.append(np.tile(pn, 4)); V.append(Me.ravel())
     n = mesh.n_pnodes
     return _scatter(np.concatenate(R), np.concatenate(C), np.concatenate(V), (n, n))
+
+
+def _pressure_tables():
+    """Bilinear basis values and derivatives (d/ds, d/dt) at the 9 Gauss points of the
+    unit square, vertex a + 2b, in the point order of reference_tables()."""
+    chi = np.zeros((9, 4)); cs = np.zeros((9, 4)); ct = np.zeros((9, 4))
+    q = 0
+    for jt in range(3):
+        for js in range(3):
+            s, t = _G[js], _G[jt]
+            ls, lt = _lin1(s), _lin1(t)
+            dl = np.array([-1.0, 1.0])
+            for b in range(2):
+                for a in range(2):
+                    chi[q, a + 2 * b] = ls[a] * lt[b]
+                    cs[q, a + 2 * b] = dl[a] * lt[b]
+                    ct[q, a + 2 * b] = ls[a] * dl[b]
+            q += 1
+    return chi, cs, ct
+
+
+def pressure_stiffness(mesh, nu_nodal):
+    """Q1 pressure-space diffusion A_p (Section 5.2, the pressure analogue of A_0):
+    [A_p]_ij = (nu grad varphi_j, grad varphi_i), nu bilinear (nodal on Q1), natural
+    boundary conditions (no boundary terms removed or added)."""
+    phi, ds, dt, chi0, w = reference_tables()
+    chi, cs, ct = _pressure_tables()
+    R, C, V = [], [], []
+    for e in range(mesh.n_elem):
+        pn = mesh.elem_q1[e]
+        nu_q = chi @ nu_nodal[pn]
+        # grad varphi = (1/h) (d/ds, d/dt); the Jacobian h^2 cancels the 1/h^2
+        Ae = np.einsum("q,qi,qj->ij", w * nu_q, cs, cs) + np.einsum("q,qi,qj->ij", w * nu_q, ct, ct)
+        R.append(np.repeat(pn, 4)); C.append(np.tile(pn, 4)); V.append(Ae.ravel())
+    n = mesh.n_pnodes
+    return _scatter(np.concatenate(R), np.concatenate(C), np.concatenate(V), (n, n))
+
+
+def pressure_convection(mesh, wx, wy):
+    """Q1 pressure-space convection N_p(w) (Section 5.2): [N_p(w)]_ij =
+    (w . grad varphi_j, varphi_i) for the Q2 field w given at all velocity nodes."""
+    phi, ds, dt, chi0, w = reference_tables()
+    chi, cs, ct = _pressure_tables()
+    h = mesh.h
+    R, C, V = [], [], []
+    for e in range(mesh.n_elem):
+        nodes = mesh.elem_q2[e]
+        pn = mesh.elem_q1[e]
+        w1 = phi @ wx[nodes]
+        w2 = phi @ wy[nodes]
+        Ne = (np.einsum("q,qi,qj->ij", w * w1, chi, cs) + np.einsum("q,qi,qj->ij", w * w2, chi, ct)) * h
+        R.append(np.repeat(pn, 4)); C.append(np.tile(pn, 4)); V.append(Ne.ravel())
+    n = mesh.n_pnodes
+    return _scatter(np.concatenate(R), np.concatenate(C), np.concatenate(V), (n, n))

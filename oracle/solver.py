@@ -194,18 +194,34 @@ class MeanLSC:
         return (u, p)
 
 
+class MeanPCD(MeanLSC):
+    """The same block triangular preconditioner with S^{-1} from the mean-based PCD
+    approximation, eq. (mean_pcd): S_PCD,0^{-1} = (B M_*^{-1} B^T)^{-1} (F_p,0 + C_p) M_p*^{-1}."""
+
+    def schur(self, ap):
+        """p = -S_PCD,0^{-1} a_p, truncated after the pressure-space mean product."""
+        d = self.d
+        _, _, mpd = d.pressure_matrices()
+        y = self._space(sp.diags(1.0 / mpd), ap)
+        y, _ = round_tt(d.apply_mean_p(self.w, y), self.eps)
+        y = self._lp_solve(y)
+        return y.scale(-1.0)
+
+
 # ---------------------------------------------------------------- Picard
-def picard(disc, tol=None, log=None):
+def picard(disc, tol=None, log=None, schur="lsc"):
     """Truncated inexact Picard iteration (Algorithm 3.1, Sections 4.2, 4.3, 5.2).
 
     Returns (u, p, stats) with u, p TTs over the free velocity / pressure dofs.
+    schur: "lsc" (eq. mean_lsc) or "pcd" (eq. mean_pcd) Schur complement approximation.
     """
+    Prec = {"lsc": MeanLSC, "pcd": MeanPCD}[schur]
     t = tol or disc.prob.tol
     fu, fp = disc.rhs()
     f = (fu, fp)
     fnorm = float(np.hypot(norm(fu), norm(fp)))
     # Stokes problem for the initial iterate (N = 0), solved to tol_gmres ||f||
-    P = MeanLSC(disc, None, t.eps_gmres, t.tol_inner, t.maxit_inner)
+    P = Prec(disc, None, t.eps_gmres, t.tol_inner, t.maxit_inner)
     (u, p), st = gmres(lambda v: disc.apply(None, *v), P, f, tol=t.tol_gmres, eps=t.eps_gmres,
                        maxit=t.maxit_gmres, space=_Pair, bnorm=fnorm)
     stats = dict(fnorm=fnorm, stokes_its=st["its"], gmres_its=[], res=[], ranks=[], conv_ranks=[],
@@ -216,7 +232,7 @@ def picard(disc, tol=None, log=None):
     while rn > t.tol_picard * fnorm and i < t.maxit_picard:
         i += 1
         wt, _ = round_tt(disc.full_velocity(u), t.eps_conv)           # eq. (eps_conv)
-        P = MeanLSC(disc, wt, t.eps_gmres, t.tol_inner, t.maxit_inner)
+        P = Prec(disc, wt, t.eps_gmres, t.tol_inner, t.maxit_inner)
         (du, dp), st = gmres(lambda v: disc.apply(wt, *v), P, r, tol=t.tol_gmres, eps=t.eps_gmres,
                              maxit=t.maxit_gmres, space=_Pair, bnorm=rn)
         u, _ = round_tt(add((1.0, u), (1.0, du)), t.eps_soln)         # eq. (eps_soln)

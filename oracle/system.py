@@ -154,6 +154,39 @@ class Discretisation:
             terms += [(1.0, self.conv_apply(w, u, mean=True))]
         return add(*terms)
 
+    # ---- pressure space (mean-based PCD, Section 5.2) ------------------------------
+    def pressure_matrices(self):
+        """M_p, A_p,0 (mean viscosity) and the diagonal of M_p (the M_p* of eq. mean_pcd),
+        assembled on first use."""
+        if not hasattr(self, "_pm"):
+            mesh = self.prob.mesh
+            Mp = fem.pressure_mass(mesh)
+            Ap0 = fem.pressure_stiffness(mesh, self.prob.nu[0])
+            self._pm = (Mp, Ap0, Mp.diagonal())
+        return self._pm
+
+    def pconv_matrix(self, w3col):
+        """N_p(w) on the pressure space for one full-node Q2 field (length 2 n_nodes)."""
+        n = self.n_nodes
+        return fem.pressure_convection(self.prob.mesh, w3col[:n], w3col[n:])
+
+    def apply_mean_p(self, w, p):
+        """(F_p,0 + C_p) p (Section 5.2): tau^-1 (I (x) I (x) M_p) p + (I (x) I (x) A_p,0) p
+        + N_p,0(w) p - tau^-1 (C (x) I (x) M_p) p, with N_p,0(w) = sum_a sum_b diag(w1_a)
+        (x) w2(a,1,b) I (x) N_p(w3_b) (w None: no convection), one term at a time."""
+        Mp, Ap0, _ = self.pressure_matrices()
+        ti = 1.0 / self.tau
+        terms = [(ti, kron_apply(None, None, Mp, p)),
+                 (1.0, kron_apply(None, None, Ap0, p)),
+                 (-ti, kron_apply(self.C, None, Mp, p))]
+        if w is not None:
+            k1, k2 = w.ranks
+            for b in range(k2):
+                Npb = self.pconv_matrix(w.z3[b])
+                for a in range(k1):
+                    terms.append((1.0, kron_apply(sp.diags(w.z1[:, a]), w.z2[a, 0, b] * np.eye(self.n_xi), Npb, p)))
+        return add(*terms)
+
     def rhs(self):
         """f = (f^u; f^p): the Dirichlet data moved to the right-hand side (linear part).
 
