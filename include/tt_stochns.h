@@ -204,8 +204,9 @@ int tt_problem_sizes(const tt_problem* prob, int* n_u, int* n_p, int* n_v, int* 
                      int* n_t, int* n_nodes);
 /* Copy out an assembled scalar matrix in CSR form over free dofs (rows) and
  * free (block 0) or Dirichlet (block 1) columns, for verification.  which:
- * 0 = M, 1 + l = A_l, 100 = B_x1, 101 = B_x2 (pressure rows).  Pass NULL
- * buffers to query nnz / rows first. */
+ * 0 = M, 1 + l = A_l, 100 = B_x1, 101 = B_x2 (pressure rows), 200 = M_p, 201 =
+ * A_p,0 (Q1 pressure space, block 0 only).  Pass NULL buffers to query nnz / rows
+ * first. */
 int tt_problem_matrix(tt_ctx* ctx, const tt_problem* prob, int which, int block,
                       int* n_rows, int* n_cols, int* nnz, int* rowptr, int* colidx,
                       double* vals);
@@ -243,7 +244,11 @@ enum {
                              replaced by a trained network (tt_net); an inner solve that
                              misses tol_inner with it within max(4, maxit_inner / 5)
                              iterations is redone with the exact K^-1 */
-    TT_PREC_PCD = 2       /* mean-based PCD, eq. (mean_pcd): not built (TT_EINVAL) */
+    TT_PREC_PCD = 2       /* mean-based PCD Schur approximation, eq. (mean_pcd):
+                             -(B M_*^-1 B^T)^-1 (F_p,0 + C_p) M_p*^-1 with the Q1
+                             pressure-space mass, mean diffusion and mean convection
+                             (natural boundary conditions), M_p* = diag(M_p); the (1,1)
+                             block as for TT_PREC_LSC */
 };
 
 typedef struct {
@@ -354,6 +359,9 @@ typedef struct {
     int rounding;           /* TT_ROUND_EXACT: every truncation by T_eps; TT_ROUND_RANDOMIZED:
                                the truncations inside GMRES (and the preconditioner) by
                                tt_round_randomized, the Picard-level ones exact */
+    int schur;              /* Schur complement approximation of the preconditioner built
+                               from these options: TT_PREC_LSC (eq. mean_lsc, 0) or
+                               TT_PREC_PCD (eq. mean_pcd); other values: TT_EINVAL */
 } tt_solver_opts;
 
 typedef struct {

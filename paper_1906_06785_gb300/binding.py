@@ -43,7 +43,7 @@ class SolverOpts(C.Structure):
     _fields_ = [("tol_picard", _D), ("tol_gmres", _D), ("eps_gmres", _D), ("eps_soln", _D),
                 ("eps_conv", _D), ("tol_inner", _D), ("maxit_picard", _I), ("maxit_gmres", _I),
                 ("maxit_inner", _I), ("precision", _I), ("learned", _P), ("init_u", _P), ("init_p", _P),
-                ("rounding", _I)]
+                ("rounding", _I), ("schur", _I)]
 
 
 class PrecOpts(C.Structure):

@@ -150,7 +150,7 @@ struct tt_prec {
     tt_op* op = nullptr;
     int kind = TT_PREC_LSC;
     tt_prec_opts o{};
-    LSCPrec make() const { return LSCPrec{c, op, o.eps, o.tol_inner, o.maxit_inner, o.net}; }
+    LSCPrec make() const { return LSCPrec{c, op, o.eps, o.tol_inner, o.maxit_inner, o.net, kind == TT_PREC_PCD}; }
 };
 
 #define API_BEGIN(ctx) \
@@ -419,6 +419,9 @@ int tt_problem_matrix(tt_ctx* ctx, const tt_problem* P, int which, int block, in
         pat = block == 0 ? &P->ff : &P->fD;
         const size_t nn = std::max(1, pat->nnz);
         v = (block == 0 ? P->A_ff.p : P->A_fD.p) + (which - 1) * nn;
+    } else if ((which == 200 || which == 201) && block == 0) {
+        pat = &P->pp;
+        v = which == 200 ? P->Mp_pp.p : P->Ap_pp.p;
     } else {
         TT_THROW(TT_EINVAL, "unknown matrix id %d", which);
     }
@@ -490,15 +493,15 @@ int tt_prec_create(tt_ctx* ctx, tt_op* op, int kind, const tt_prec_opts* o, tt_p
     *out = nullptr;
     TT_REQUIRE(op->which == TT_OP_FULL, "a preconditioner needs a FULL operator");
     TT_REQUIRE(o->maxit_inner >= 1 && o->maxit_inner <= 63, "maxit_inner must be in [1, 63]");
-    if (kind == TT_PREC_PCD) TT_THROW(TT_EINVAL, "the mean-based PCD preconditioner is not built");
-    TT_REQUIRE(kind == TT_PREC_LSC || kind == TT_PREC_LEARNED, "unknown preconditioner kind %d", kind);
-    TT_REQUIRE(kind == TT_PREC_LSC || o->net, "TT_PREC_LEARNED needs a network");
+    TT_REQUIRE(kind == TT_PREC_LSC || kind == TT_PREC_LEARNED || kind == TT_PREC_PCD,
+               "unknown preconditioner kind %d", kind);
+    TT_REQUIRE(kind != TT_PREC_LEARNED || o->net, "TT_PREC_LEARNED needs a network");
     tt_prec* pr = new tt_prec;
     pr->c = ctx;
     pr->op = op;
     pr->kind = kind;
     pr->o = *o;
-    if (kind == TT_PREC_LSC) pr->o.net = nullptr;
+    if (kind != TT_PREC_LEARNED) pr->o.net = nullptr;
     *out = pr;
     API_END
 }
@@ -545,7 +548,10 @@ int tt_gmres(tt_ctx* ctx, tt_op* op, tt_prec* prec, const tt_solver_opts* o, con
     TT_REQUIRE(op->which == TT_OP_FULL, "tt_gmres needs a FULL operator");
     TT_REQUIRE(o->precision == TT_FP64 || o->precision == TT_MIXED, "unknown precision %d", o->precision);
     TT_REQUIRE(!prec || prec->op == op, "the preconditioner belongs to another operator");
-    LSCPrec pre = prec ? prec->make() : LSCPrec{ctx, op, o->eps_gmres, o->tol_inner, o->maxit_inner, o->learned};
+    TT_REQUIRE(o->schur == TT_PREC_LSC || o->schur == TT_PREC_PCD, "schur must be TT_PREC_LSC or TT_PREC_PCD");
+    LSCPrec pre = prec ? prec->make()
+                       : LSCPrec{ctx, op, o->eps_gmres, o->tol_inner, o->maxit_inner, o->learned,
+                                 o->schur == TT_PREC_PCD};
     Vec b;
     b.u = clone(ctx, bu);
     b.p = clone(ctx, bp);

@@ -20,6 +20,8 @@ __constant__ double c_phi[9][9];   // [q][i]
 __constant__ double c_ds[9][9];
 __constant__ double c_dt[9][9];
 __constant__ double c_chi[9][4];
+__constant__ double c_chs[9][4];   // d chi / ds (bilinear pressure basis)
+__constant__ double c_cht[9][4];   // d chi / dt
 __constant__ double c_w[9];
 
 static void upload_tables() {
@@ -29,7 +31,7 @@ static void upload_tables() {
         return a == 0 ? 2.0 * (s - 0.5) * (s - 1.0) : (a == 1 ? 4.0 * s * (1.0 - s) : 2.0 * s * (s - 0.5));
     };
     auto dL = [](int a, double s) { return a == 0 ? 4.0 * s - 3.0 : (a == 1 ? 4.0 - 8.0 * s : 4.0 * s - 1.0); };
-    double phi[9][9], ds[9][9], dt[9][9], chi[9][4], w[9];
+    double phi[9][9], ds[9][9], dt[9][9], chi[9][4], chs[9][4], cht[9][4], w[9];
     for (int qt = 0; qt < 3; ++qt)
         for (int qs = 0; qs < 3; ++qs) {
             const int q = qs + 3 * qt;
@@ -42,13 +44,18 @@ static void upload_tables() {
                     dt[q][a + 3 * b] = L(a, s) * dL(b, t);
                 }
             for (int b = 0; b < 2; ++b)
-                for (int a = 0; a < 2; ++a)
+                for (int a = 0; a < 2; ++a) {
                     chi[q][a + 2 * b] = (a ? s : 1.0 - s) * (b ? t : 1.0 - t);
+                    chs[q][a + 2 * b] = (a ? 1.0 : -1.0) * (b ? t : 1.0 - t);
+                    cht[q][a + 2 * b] = (a ? s : 1.0 - s) * (b ? 1.0 : -1.0);
+                }
         }
     CUDA_CHECK(cudaMemcpyToSymbol(c_phi, phi, sizeof(phi)));
     CUDA_CHECK(cudaMemcpyToSymbol(c_ds, ds, sizeof(ds)));
     CUDA_CHECK(cudaMemcpyToSymbol(c_dt, dt, sizeof(dt)));
     CUDA_CHECK(cudaMemcpyToSymbol(c_chi, chi, sizeof(chi)));
+    CUDA_CHECK(cudaMemcpyToSymbol(c_chs, chs, sizeof(chs)));
+    CUDA_CHECK(cudaMemcpyToSymbol(c_cht, cht, sizeof(cht)));
     CUDA_CHECK(cudaMemcpyToSymbol(c_w, w, sizeof(w)));
 }
 
@@ -119,6 +126,59 @@ __global__ void k_local_div(int n_elem, double h, double* __restrict__ loc) {
     loc[((size_t)c * n_elem + e) * 36 + t] = -s * h;
 }
 
+// Q1 pressure-space element matrices (Section 5.2, the pressure analogues of M, A_0
+// and N(w) for the PCD approximation), 16 entries per element, local vertex a + 2b:
+//   mass:       h^2 sum_q w chi_i chi_j
+//   diffusion:  sum_q w nu_q (dchi_i/ds dchi_j/ds + dchi_i/dt dchi_j/dt)   (nu row 0: mean)
+//   convection: h sum_q w (w1 dchi_j/ds + w2 dchi_j/dt) chi_i, w the Q2 field f
+__global__ void k_local_pmat(int n_elem, int n_p, double h, const int* __restrict__ eq1, const double* __restrict__ nu,
+                             double* __restrict__ loc) {
+    const int e = blockIdx.x, kind = blockIdx.y, t = threadIdx.x;
+    __shared__ double nuq[9];
+    if (t < 9) {
+        double v = 0.0;
+        for (int p = 0; p < 4; ++p) v += c_chi[t][p] * nu[eq1[e * 4 + p]];
+        nuq[t] = v;
+    }
+    __syncthreads();
+    if (t >= 16) return;
+    const int i = t / 4, j = t % 4;
+    double s = 0.0;
+    if (kind == 0) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) s += c_w[q] * c_chi[q][i] * c_chi[q][j];
+        s *= h * h;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) s += c_w[q] * nuq[q] * (c_chs[q][i] * c_chs[q][j] + c_cht[q][i] * c_cht[q][j]);
+    }
+    loc[((size_t)kind * n_elem + e) * 16 + t] = s;
+}
+
+__global__ void k_local_pconv(int n_elem, int n_nodes, double h, const int* __restrict__ eq2,
+                              const double* __restrict__ W, int ldw, double* __restrict__ loc) {
+    const int e = blockIdx.x, f = blockIdx.y, t = threadIdx.x;
+    __shared__ double wn[2][9], wq[2][9];
+    if (t < 18) {
+        const int c = t / 9, a = t % 9;
+        wn[c][a] = W[((size_t)c * n_nodes + eq2[e * 9 + a]) * ldw + f];
+    }
+    __syncthreads();
+    if (t < 18) {
+        const int c = t / 9, q = t % 9;
+        double v = 0.0;
+        for (int a = 0; a < 9; ++a) v += c_phi[q][a] * wn[c][a];
+        wq[c][q] = v;
+    }
+    __syncthreads();
+    if (t >= 16) return;
+    const int i = t / 4, j = t % 4;
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) s += c_w[q] * (wq[0][q] * c_chs[q][j] + wq[1][q] * c_cht[q][j]) * c_chi[q][i];
+    loc[((size_t)f * n_elem + e) * 16 + t] = s * h;
+}
+
 // vals[f*nnz + s] = sum_{t in gather(s)} loc[f*L + idx[t]]
 __global__ void k_gather(int nnz, int nf, long long L, const int* __restrict__ ptr, const int* __restrict__ idx,
                          const double* __restrict__ loc, double* __restrict__ vals) {
@@ -176,7 +236,7 @@ template <typename TC>
 __global__ void __launch_bounds__(256)
 k_spmm_vel(VelSpmm s, const double* __restrict__ X, int ldx, double* __restrict__ Y, int ldy, int ncol) {
     const int wg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (wg >= 2 * s.n_rows) return;
+    if (wg >= s.ncomp * s.n_rows) return;
     const int comp = wg / s.n_rows, i = wg % s.n_rows;
     const double* Xc = X + (size_t)comp * s.n_in * ldx;
     double* Yr = Y + ((size_t)comp * s.n_rows + i) * ldy;
@@ -239,12 +299,13 @@ __global__ void k_spmm_grad(int n_rows, const int* __restrict__ rp, const int* _
 
 void spmm_vel(tt_ctx* c, const VelSpmm& s, const double* X, int ldx, double* Y, int ldy, int ncol) {
     TT_REQUIRE(s.nmat >= 1 && s.nmat <= 8, "spmm_vel: nmat %d", s.nmat);
-    const long long threads = 2LL * s.n_rows * 32;
+    TT_REQUIRE(s.ncomp == 1 || s.ncomp == 2, "spmm_vel: ncomp %d", s.ncomp);
+    const long long threads = (long long)s.ncomp * s.n_rows * 32;
     // algorithmic bytes: pattern + nmat value arrays once, X once, Y once
     const double nnz = s.nnz;
-    ProfScope prof(c, PROF_SPMM, 4.0 * nnz * ncol * s.nmat,
-                   (double)nnz * (4 + 8 * s.nmat) + 4.0 * (s.n_rows + 1) + 8.0 * 2 * s.n_in * ncol +
-                       8.0 * 2 * s.n_rows * ncol * s.nmat);
+    ProfScope prof(c, PROF_SPMM, 2.0 * s.ncomp * nnz * ncol * s.nmat,
+                   (double)nnz * (4 + 8 * s.nmat) + 4.0 * (s.n_rows + 1) + 8.0 * s.ncomp * s.n_in * ncol +
+                       8.0 * s.ncomp * s.n_rows * ncol * s.nmat);
     (c->fast ? k_spmm_vel<float> : k_spmm_vel<double>)<<<ceil_div(threads, 256), 256, 0, c->stream>>>(
         s, X, ldx, Y, ldy, ncol);
     LAUNCH_CHECK(c);
@@ -397,6 +458,14 @@ void assemble_conv(tt_ctx* c, tt_problem* P, const double* W, int ldw, int nf, d
     if (vals_fD) gather_vals(c, P->fD, P->g_fD, nf, (long long)P->n_elem * 81, loc.p, vals_fD);
 }
 
+void assemble_pconv(tt_ctx* c, tt_problem* P, const double* W, int ldw, int nf, double* vals_pp) {
+    if (nf <= 0) return;
+    DBuf<double> loc(c, (size_t)nf * P->n_elem * 16);
+    k_local_pconv<<<dim3(P->n_elem, nf), 32, 0, c->stream>>>(P->n_elem, P->n_nodes, P->h, P->eq2.p, W, ldw, loc.p);
+    LAUNCH_CHECK(c);
+    gather_vals(c, P->pp, P->g_pp, nf, (long long)P->n_elem * 16, loc.p, vals_pp);
+}
+
 void scatter_band(tt_ctx* c, tt_problem* P, const double* vals, double* ab) {
     k_scatter_band<<<ceil_div(P->n_v, 256), 256, 0, c->stream>>>(P->n_v, P->bwK, P->ff.rowptr.p, P->ff.col.p, vals, ab);
     LAUNCH_CHECK(c);
@@ -546,8 +615,8 @@ void build_problem(tt_ctx* c, tt_problem* P, const tt_problem_desc* d) {
     }
 
     // ---- patterns and gather maps
-    std::vector<std::vector<int>> cff(nf), cfD(nf), cBF(np_), cBD(np_);
-    std::vector<std::vector<std::pair<int, int>>> lff(nf), lfD(nf), lBF(np_), lBD(np_);
+    std::vector<std::vector<int>> cff(nf), cfD(nf), cBF(np_), cBD(np_), cpp(np_);
+    std::vector<std::vector<std::pair<int, int>>> lff(nf), lfD(nf), lBF(np_), lBD(np_), lpp(np_);
     for (int e = 0; e < E; ++e) {
         for (int i = 0; i < 9; ++i) {
             const int ri = P->fidx[q2[e * 9 + i]];
@@ -558,6 +627,11 @@ void build_problem(tt_ctx* c, tt_problem* P, const tt_problem_desc* d) {
                 else { cfD[ri].push_back(P->didx[nj]); lfD[ri].push_back({P->didx[nj], e * 81 + i * 9 + j}); }
             }
         }
+        for (int p = 0; p < 4; ++p)
+            for (int p2 = 0; p2 < 4; ++p2) {
+                cpp[q1[e * 4 + p]].push_back(q1[e * 4 + p2]);
+                lpp[q1[e * 4 + p]].push_back({q1[e * 4 + p2], e * 16 + p * 4 + p2});
+            }
         for (int p = 0; p < 4; ++p) {
             const int rp = q1[e * 4 + p];
             for (int j = 0; j < 9; ++j) {
@@ -570,11 +644,25 @@ void build_problem(tt_ctx* c, tt_problem* P, const tt_problem_desc* d) {
     auto uniq = [](std::vector<std::vector<int>>& v) {
         for (auto& r : v) { std::sort(r.begin(), r.end()); r.erase(std::unique(r.begin(), r.end()), r.end()); }
     };
-    uniq(cff); uniq(cfD); uniq(cBF); uniq(cBD);
+    uniq(cff); uniq(cfD); uniq(cBF); uniq(cBD); uniq(cpp);
     build_gather(lff, cff, P->ff, P->g_ff, nf, c);
     build_gather(lfD, cfD, P->fD, P->g_fD, nd, c);
     build_gather(lBF, cBF, P->BF, P->g_BF, nf, c);
     build_gather(lBD, cBD, P->BD, P->g_BD, nd, c);
+    build_gather(lpp, cpp, P->pp, P->g_pp, np_, c);
+    {
+        // diagonal slots of the pressure pattern
+        std::vector<int> dslot(np_), prp(np_ + 1, 0);
+        for (int i = 0; i < np_; ++i) prp[i + 1] = prp[i] + (int)cpp[i].size();
+        for (int i = 0; i < np_; ++i) {
+            const auto it = std::lower_bound(cpp[i].begin(), cpp[i].end(), i);
+            TT_REQUIRE(it != cpp[i].end() && *it == i, "missing diagonal in the pressure pattern");
+            dslot[i] = prp[i] + (int)(it - cpp[i].begin());
+        }
+        P->pdiag_slot.alloc(c, np_);
+        CUDA_CHECK(cudaMemcpyAsync(P->pdiag_slot.p, dslot.data(), np_ * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+        CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    }
     // bandwidths
     int bw = 0;
     for (int i = 0; i < nf; ++i)
@@ -659,6 +747,22 @@ void build_problem(tt_ctx* c, tt_problem* P, const tt_problem_desc* d) {
         k_take<<<ceil_div(P->BT.nnz, 256), 256, 0, c->stream>>>(P->BT.nnz, P->bt_perm.p, P->Bx_F.p, P->BTx.p);
         LAUNCH_CHECK(c);
         k_take<<<ceil_div(P->BT.nnz, 256), 256, 0, c->stream>>>(P->BT.nnz, P->bt_perm.p, P->By_F.p, P->BTy.p);
+        LAUNCH_CHECK(c);
+    }
+    {
+        // pressure-space mass and mean diffusion (Section 5.2), and M_p* = diag(M_p)
+        DBuf<double> loc(c, (size_t)2 * E * 16);
+        k_local_pmat<<<dim3(E, 2), 32, 0, c->stream>>>(E, np_, P->h, P->eq1.p, P->nu.p, loc.p);
+        LAUNCH_CHECK(c);
+        DBuf<double> pv(c, (size_t)2 * std::max(1, P->pp.nnz));
+        gather_vals(c, P->pp, P->g_pp, 2, (long long)E * 16, loc.p, pv.p);
+        P->Mp_pp.alloc(c, std::max(1, P->pp.nnz));
+        P->Ap_pp.alloc(c, std::max(1, P->pp.nnz));
+        CUDA_CHECK(cudaMemcpyAsync(P->Mp_pp.p, pv.p, P->pp.nnz * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        CUDA_CHECK(cudaMemcpyAsync(P->Ap_pp.p, pv.p + P->pp.nnz, P->pp.nnz * sizeof(double), cudaMemcpyDeviceToDevice,
+                                   c->stream));
+        P->Mpstar.alloc(c, np_);
+        k_take<<<ceil_div(np_, 256), 256, 0, c->stream>>>(np_, P->pdiag_slot.p, P->Mp_pp.p, P->Mpstar.p);
         LAUNCH_CHECK(c);
     }
     P->Mstar.alloc(c, nf);

@@ -676,6 +676,7 @@ int tt_net_train(tt_ctx* ctx, tt_net* net, tt_op* op, const double* R, int count
             if (start >= count) break;
             VelSpmm s{};
             s.rowptr = P->ff.rowptr.p; s.col = P->ff.col.p; s.n_rows = nv; s.n_in = nv; s.nnz = P->ff.nnz;
+            s.ncomp = 2;
             s.nmat = 1; s.vals[0] = kv.p; s.coef[0] = 1.0; s.coff[0] = 0;
             PrecScope fp64(ctx, 0);
             spmm_vel(ctx, s, dR.p + start, count, KX.p + start, count, count - start);

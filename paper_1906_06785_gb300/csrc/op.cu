@@ -101,7 +101,8 @@ __global__ void k_embed(int n_in, int n_nodes, int r, const int* __restrict__ ma
 
 static int out_rows(tt_problem* P, SKind k, const tt_t* in) {
     switch (k) {
-        case S_COPY: case S_MSTARINV: case S_SOLVE_K: case S_SOLVE_LP: return in->n_x;
+        case S_COPY: case S_MSTARINV: case S_SOLVE_K: case S_SOLVE_LP: case S_MPSTARINV: return in->n_x;
+        case S_PRES: return P->n_p;
         case S_VEL: case S_VELD: case S_GRAD: return 2 * P->n_v;
         case S_DIV: case S_DIVD: return P->n_p;
         case S_EMBED_F: case S_EMBED_D: return 2 * P->n_nodes;
@@ -114,7 +115,7 @@ static void check_in_rows(tt_problem* P, SKind k, const tt_t* in) {
     switch (k) {
         case S_VEL: case S_DIV: case S_MSTARINV: case S_SOLVE_K: case S_EMBED_F: need = 2 * P->n_v; break;
         case S_VELD: case S_DIVD: case S_EMBED_D: need = 2 * P->n_D; break;
-        case S_GRAD: case S_SOLVE_LP: need = P->n_p; break;
+        case S_GRAD: case S_SOLVE_LP: case S_PRES: case S_MPSTARINV: need = P->n_p; break;
         default: break;
     }
     TT_REQUIRE(need < 0 || in->n_x == need, "spatial operator %d expects %d rows, train has %d", (int)k, need, in->n_x);
@@ -188,11 +189,13 @@ TTPtr kron_sum(tt_ctx* c, tt_problem* P, const std::vector<C1>& b1, const std::v
             if (done[i]) continue;
             const C3& q = b3[i];
             const tt_t* in = q.in;
-            if (q.kind == S_VEL || q.kind == S_VELD) {
-                const Csr& pat = q.kind == S_VEL ? P->ff : P->fD;
+            if (q.kind == S_VEL || q.kind == S_VELD || q.kind == S_PRES) {
+                const Csr& pat = q.kind == S_VEL ? P->ff : q.kind == S_VELD ? P->fD : P->pp;
                 VelSpmm s{};
-                s.rowptr = pat.rowptr.p; s.col = pat.col.p; s.n_rows = P->n_v; s.nnz = pat.nnz;
-                s.n_in = q.kind == S_VEL ? P->n_v : P->n_D;
+                s.rowptr = pat.rowptr.p; s.col = pat.col.p; s.nnz = pat.nnz;
+                s.n_rows = q.kind == S_PRES ? P->n_p : P->n_v;
+                s.n_in = q.kind == S_VEL ? P->n_v : q.kind == S_VELD ? P->n_D : P->n_p;
+                s.ncomp = q.kind == S_PRES ? 1 : 2;
                 s.nmat = 0;
                 for (size_t j = i; j < b3.size(); ++j) {
                     if (done[j] || b3[j].in != in || b3[j].kind != q.kind) continue;
@@ -212,9 +215,11 @@ TTPtr kron_sum(tt_ctx* c, tt_problem* P, const std::vector<C1>& b1, const std::v
             switch (q.kind) {
                 case S_COPY:
                 case S_MSTARINV:
+                case S_MPSTARINV:
                     k_core3_copy<<<std::min(4096, ceil_div(tot, 256)), 256, 0, c->stream>>>(
                         in->n_x, in->r2, in->z3, out->z3, R2, off3[i], q.coef,
-                        q.kind == S_MSTARINV ? P->Mstar.p : nullptr, P->n_v);
+                        q.kind == S_MSTARINV ? P->Mstar.p : q.kind == S_MPSTARINV ? P->Mpstar.p : nullptr,
+                        q.kind == S_MPSTARINV ? P->n_p : P->n_v);
                     LAUNCH_CHECK(c);
                     break;
                 case S_DIV:
@@ -430,6 +435,33 @@ void op_apply_mean(tt_ctx* c, const tt_op* op, const tt_t* u, TTPtr* ou) {
         }
     }
     *ou = kron_sum(c, P, b1, b3, b2);
+}
+
+void op_apply_mean_p(tt_ctx* c, tt_op* op, const tt_t* p, TTPtr* out) {
+    tt_problem* P = op->P;
+    TT_REQUIRE(p->n_x == P->n_p, "pressure mean matvec: p size does not match the problem");
+    const double ti = 1.0 / P->tau;
+    if (op->w && !op->pready) {
+        // N_p(w3_b) for the columns of the convection field's last core
+        const size_t nnz = std::max(1, P->pp.nnz);
+        op->Npp.alloc(c, (size_t)op->kw2 * nnz);
+        assemble_pconv(c, P, op->w->z3, op->kw2, op->kw2, op->Npp.p);
+        op->pready = true;
+    }
+    // tau^-1 (I - C) (x) I (x) M_p + I (x) I (x) A_p,0 + N_p,0(w), with
+    // N_p,0(w) = sum_b diag(c_b) (x) I (x) N_p(w3_b), c_b(t) = sum_a w1(t,a) w2(a,0,b)
+    std::vector<C1> b1 = {C1{p, T_COPY, nullptr}, C1{p, T_SHIFT, nullptr}};
+    std::vector<C3> b3 = {C3{p, S_PRES, P->Mp_pp.p, 1.0}, C3{p, S_PRES, P->Ap_pp.p, 1.0}};
+    std::vector<C2> b2 = {C2{0, 0, nullptr, ti, nullptr}, C2{1, 0, nullptr, -ti, nullptr}, C2{0, 1, nullptr, 1.0, nullptr}};
+    if (op->w) {
+        const size_t nnz = std::max(1, P->pp.nnz);
+        for (int b = 0; b < op->kw2; ++b) {
+            b1.push_back(C1{p, T_DIAG, op->cmean.p + (size_t)b * P->n_t});
+            b3.push_back(C3{p, S_PRES, op->Npp.p + b * nnz, 1.0});
+            b2.push_back(C2{(int)b1.size() - 1, (int)b3.size() - 1, nullptr, 1.0, nullptr});
+        }
+    }
+    *out = kron_sum(c, P, b1, b3, b2);
 }
 
 // ============================================================== residual

@@ -18,7 +18,9 @@ enum SKind {
     S_SOLVE_K,   // banded K^{-1} on both components (band = factor)
     S_SOLVE_LP,  // banded L_p^{-1} (problem's factor)
     S_EMBED_F,   // free velocity dofs -> full-node field (2 n_nodes rows)
-    S_EMBED_D    // Dirichlet dofs -> full-node field
+    S_EMBED_D,   // Dirichlet dofs -> full-node field
+    S_PRES,      // scalar pressure-space matrix (vals on P->pp): n_p -> n_p
+    S_MPSTARINV  // M_p*^{-1} = diag(M_p)^{-1} on a pressure train
 };
 struct C1 {            // core-1 block: time operator on an input's first core
     const tt_t* in;
@@ -62,6 +64,8 @@ struct tt_op {
     tt::DBuf<double> cmean;   // n_t x kw2, column-major: c_b(t) = sum_a w1(t,a) w2(a,0,b)
     tt::DBuf<double> Kband;   // factorised tau^-1 M + A_0 + N(w_avg)
     bool kready = false;
+    tt::DBuf<double> Npp;     // kw2 x nnz(pp): N_p(w3_b) on the pressure space (PCD)
+    bool pready = false;
 };
 
 namespace tt {
@@ -69,6 +73,8 @@ void op_init(tt_ctx* c, tt_op* op, tt_problem* P, const tt_t* w, int which);
 // L[u; p] (FULL) or (F_0 + C) u (MEAN) without truncation
 void op_apply(tt_ctx* c, const tt_op* op, const tt_t* u, const tt_t* p, TTPtr* ou, TTPtr* op_);
 void op_apply_mean(tt_ctx* c, const tt_op* op, const tt_t* u, TTPtr* ou);
+// (F_p,0 + C_p) p on the pressure space (Section 5.2) without truncation
+void op_apply_mean_p(tt_ctx* c, tt_op* op, const tt_t* p, TTPtr* out);
 void op_ensure_K(tt_ctx* c, tt_op* op);
 // w_avg of eq. (11_prec) (full-node, 2 n_nodes values) into out; zeros and false
 // when the operator has no convection field

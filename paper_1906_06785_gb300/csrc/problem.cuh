@@ -17,11 +17,12 @@ struct Gather {
 
 // Sparse kernels --------------------------------------------------------------
 // Y[(c*n_rows + i)*ldy + coff[k] + b] = coef[k] * sum_nz vals[k][nz] X[(c*n_in + col)*ldx + b]
-// for both velocity components c, k < nmat (<= 8), b < ncol.
+// for components c < ncomp (both velocity components, or one), k < nmat (<= 8), b < ncol.
 struct VelSpmm {
     const int* rowptr;
     const int* col;
     int n_rows, n_in;
+    int ncomp;          // components (2: velocity; 1: a scalar pressure-space matrix)
     int nnz;
     int nmat;
     const double* vals[8];
@@ -53,8 +54,8 @@ struct tt_problem {
     tt::DBuf<int> eq2, eq1;                 // element connectivity
     tt::DBuf<int> node_free, node_dir;      // device copies of fidx / didx
     tt::DBuf<int> free_nodes, dir_nodes;    // free / Dirichlet index -> node
-    tt::Csr ff, fD, BF, BD, BT;             // patterns
-    tt::Gather g_ff, g_fD, g_BF, g_BD;      // assembly gather maps
+    tt::Csr ff, fD, BF, BD, BT, pp;         // patterns (pp: Q1 pressure space)
+    tt::Gather g_ff, g_fD, g_BF, g_BD, g_pp;  // assembly gather maps
     tt::DBuf<int> bt_perm;                  // BT slot -> BF slot
     tt::DBuf<int> diag_slot;                // ff slot of (i, i)
     tt::DBuf<double> nu;                    // (m+1) x n_p nodal viscosities
@@ -62,6 +63,9 @@ struct tt_problem {
     tt::DBuf<double> A_ff, A_fD;            // (m+1) x nnz
     tt::DBuf<double> Bx_F, By_F, Bx_D, By_D, BTx, BTy;
     tt::DBuf<double> Mstar;                 // diag of M_ff (n_v)
+    tt::DBuf<int> pdiag_slot;               // pp slot of (i, i)
+    tt::DBuf<double> Mp_pp, Ap_pp;          // pressure mass, mean pressure diffusion (pp)
+    tt::DBuf<double> Mpstar;                // diag of M_p (n_p)
     tt::DBuf<double> G;                     // (m+1) x n_xi x n_xi
     tt::DBuf<double> H;                     // n_xi x n_xi x n_xi  H[l][r][s]
     std::vector<double> hG;                 // host copy of G
@@ -80,6 +84,8 @@ namespace tt {
 // w_k(node) = (W[(node)*ldw + col_k], W[(n_nodes + node)*ldw + col_k]) with col_k = k.
 void assemble_conv(tt_ctx* c, tt_problem* P, const double* W, int ldw, int nf, double* vals_ff,
                    double* vals_fD);
+// Pressure-space convection N_p(w) values on the pp pattern for nf fields (as above)
+void assemble_pconv(tt_ctx* c, tt_problem* P, const double* W, int ldw, int nf, double* vals_pp);
 // Values of K = tau^-1 M + A_0 + N(w) on the ff pattern (w full-node field or null)
 void assemble_K_vals(tt_ctx* c, tt_problem* P, const double* wfield, double* kv);
 // K = tau^-1 M + A_0 + N(w) scattered into band storage and factorised (LU)

@@ -175,7 +175,18 @@ TTPtr LSCPrec::minv(const tt_t* z) {
                     {C2{0, 0, nullptr, 1.0, nullptr}});
 }
 
+TTPtr LSCPrec::schur_pcd(const tt_t* ap) {
+    // p = -L^-1 (F_p,0 + C_p) M_p*^-1 a_p  (eq. mean_pcd), L = B M*^-1 B^T
+    tt_problem* P = op->P;
+    TTPtr y = apply_space(c, P, ap, S_MPSTARINV);
+    TTPtr fy{nullptr, tt_free};
+    op_apply_mean_p(c, op, y.get(), &fy);
+    y = round_any(c, fy.get(), eps);
+    return apply_space(c, P, y.get(), S_SOLVE_LP, -1.0);
+}
+
 TTPtr LSCPrec::schur(const tt_t* ap) {
+    if (pcd) return schur_pcd(ap);
     // p = -L^-1 (B M*^-1 (F_0 + C) M*^-1 B^T) L^-1 a_p  (eq. mean_lsc), L = B M*^-1 B^T
     tt_problem* P = op->P;
     TTPtr y = apply_space(c, P, ap, S_SOLVE_LP);
@@ -240,6 +251,7 @@ void picard(tt_ctx* c, tt_problem* P, const tt_solver_opts* o, TTPtr* uo, TTPtr*
     TT_REQUIRE(o->rounding == TT_ROUND_EXACT || o->rounding == TT_ROUND_RANDOMIZED, "unknown rounding %d",
                o->rounding);
     TT_REQUIRE((o->init_u == nullptr) == (o->init_p == nullptr), "init_u and init_p go together");
+    TT_REQUIRE(o->schur == TT_PREC_LSC || o->schur == TT_PREC_PCD, "schur must be TT_PREC_LSC or TT_PREC_PCD");
     memset(st, 0, sizeof(*st));
     st->fnorm = P->fnorm;
     const int fast = o->precision == TT_MIXED ? 1 : 0;
@@ -258,7 +270,7 @@ void picard(tt_ctx* c, tt_problem* P, const tt_solver_opts* o, TTPtr* uo, TTPtr*
         // Stokes problem (N = 0) for the initial iterate, solved to tol_gmres ||f|| (Section 5.2)
         tt_op stokes;
         op_init(c, &stokes, P, nullptr, TT_OP_FULL);
-        LSCPrec pre{c, &stokes, o->eps_gmres, o->tol_inner, o->maxit_inner, o->learned};
+        LSCPrec pre{c, &stokes, o->eps_gmres, o->tol_inner, o->maxit_inner, o->learned, o->schur == TT_PREC_PCD};
         GmresOut go;
         Vec up;
         {
@@ -287,7 +299,7 @@ void picard(tt_ctx* c, tt_problem* P, const tt_solver_opts* o, TTPtr* uo, TTPtr*
         st->conv_ranks[i][0] = wt->r1; st->conv_ranks[i][1] = wt->r2;
         tt_op L;
         op_init(c, &L, P, wt.get(), TT_OP_FULL);
-        LSCPrec pr{c, &L, o->eps_gmres, o->tol_inner, o->maxit_inner, o->learned};
+        LSCPrec pr{c, &L, o->eps_gmres, o->tol_inner, o->maxit_inner, o->learned, o->schur == TT_PREC_PCD};
         Vec r;
         r.u = std::move(ru);
         r.p = std::move(rp);

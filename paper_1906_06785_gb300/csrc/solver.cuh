@@ -35,10 +35,12 @@ struct LSCPrec {
     double eps, tol_inner;
     int maxit_inner;
     const tt_net* net = nullptr;
+    bool pcd = false;       // Schur part from eq. (mean_pcd) instead of eq. (mean_lsc)
     int inner_its = 0;
     int fallbacks = 0;
     Vec apply(const Vec& v);
     TTPtr schur(const tt_t* ap);
+    TTPtr schur_pcd(const tt_t* ap);
     TTPtr minv(const tt_t* z);
 };
 

@@ -113,8 +113,8 @@ def test_preconditioner_kinds(ctx, binding):
     prob = synth.preset("tiny")
     P = ctx.problem(prob)
     op = P.op(None)
-    with pytest.raises(binding.LibraryError, match="PCD"):
-        op.make_prec(binding.PREC_PCD, 1e-8, 1e-1, 10)
+    with pytest.raises(binding.LibraryError, match="kind"):
+        op.make_prec(7, 1e-8, 1e-1, 10)
     with pytest.raises(binding.LibraryError, match="network"):
         op.make_prec(binding.PREC_LEARNED, 1e-8, 1e-1, 10)
     fu, fp = P.rhs()
