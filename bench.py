@@ -72,10 +72,10 @@ def _args():
                     help="op-level run on the workload's shapes (default large: n_u=22144, n_xi=56, n_t=400): "
                          "TT matvec of the full operator and the truncation of its output, per kernel class "
                          "achieved GB/s and TFLOP/s; prints one JSON line")
-    ap.add_argument("--study", default="", choices=["", "table53", "sweep"],
+    ap.add_argument("--study", default="", choices=["", "table53", "sweep", "prec"],
                     help="table53: the paper problem (Table 5.1) with the three GMRES tolerances of Table 5.3; "
-                         "sweep: the paper problem over element sizes h and time steps tau (Fig. 5.6); one JSON "
-                         "line per solve")
+                         "sweep: the paper problem over element sizes h and time steps tau (Fig. 5.6); prec: LSC "
+                         "against PCD Schur approximations at h = 1/4 and 1/8 (Fig. 5.4); one JSON line per solve")
     ap.add_argument("--solves-only", dest="solves_only", action="store_true",
                     help="profiling run: W warm + K solves of the headline precision and nothing else; prints "
                          "the kernel launches of each solve (for ncu -s / -c)")
@@ -588,7 +588,8 @@ def run_study(a):
     Table 5.2 tolerances, FP64 and the LSC preconditioner as in the paper:
       table53: tol_gmres in {1e-1, 1e-3, 1e-5} with eps_gmres = 1e-2 tol_gmres (Table 5.3);
       sweep:   element size h in {1/2, 1/4, 1/8} at n_t = 64, and n_t in {16, 32, 64, 128}
-               (tau = 1 / n_t) at h = 1/4 (Fig. 5.6).
+               (tau = 1 / n_t) at h = 1/4 (Fig. 5.6);
+      prec:    the mean-based LSC and PCD Schur approximations at h = 1/4 and 1/8 (Fig. 5.4).
     Each solve is timed once with CUDA events (after a warm-up solve of the first case)."""
     import torch
     import synth
@@ -598,6 +599,9 @@ def run_study(a):
     if a.study == "table53":
         cases = [dict(label=f"tol_gmres={tg:g}", over={}, tol=dict(tol_gmres=tg, eps_gmres=1e-2 * tg))
                  for tg in (1e-1, 1e-3, 1e-5)]
+    elif a.study == "prec":
+        cases = [dict(label=f"h={h:g} {sc}", over=dict(h=h), tol={}, schur=sc)
+                 for h in (0.25, 0.125) for sc in ("lsc", "pcd")]
     else:
         cases = [dict(label=f"h={h:g}", over=dict(h=h), tol={}) for h in (0.5, 0.25, 0.125)]
         cases += [dict(label=f"n_t={nt}", over=dict(n_t=nt, tau=1.0 / nt), tol={}) for nt in (16, 32, 64, 128)]
@@ -607,7 +611,8 @@ def run_study(a):
         for k, v in cs["tol"].items():
             setattr(prob.tol, k, v)
         P = ctx.problem(prob)
-        o = binding.opts_from(prob.tol, precision=binding.FP64)
+        o = binding.opts_from(prob.tol, precision=binding.FP64,
+                              schur=binding.PREC_PCD if cs.get("schur") == "pcd" else binding.PREC_LSC)
         if warm:
             P.picard(o)
             warm = False
@@ -624,6 +629,7 @@ def run_study(a):
                           "picard_its": n, "gmres_its_total": int(sum(st.gmres_its[1:n + 1])),
                           "gmres_its": list(st.gmres_its[1:n + 1]), "stokes_its": st.stokes_its,
                           "rel_res": st.res[n] / st.fnorm, "u_ranks": u.ranks, "p_ranks": p.ranks,
+                          "schur": cs.get("schur", "lsc"), "inner_its": list(st.inner_its[:n + 1]),
                           "seconds": e0.elapsed_time(e1) / 1000.0}), flush=True)
         del u, p, P
 
