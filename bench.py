@@ -82,6 +82,10 @@ def _args():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="mixed: FP32 SpMM/GEMM/R factors inside GMRES, FP64 SVDs, dots, residual; "
                          "fp64: plain FP64 throughout")
+    ap.add_argument("--maxit-picard", dest="maxit_picard", type=int, default=0,
+                    help="with --solves-only: stop after this many Picard steps (0: the workload's own cap)")
+    ap.add_argument("--rounding", default="exact", choices=["exact", "randomized"],
+                    help="with --solves-only: truncation inside GMRES")
     return ap.parse_args()
 
 
@@ -643,15 +647,28 @@ def run_solves_only(a):
     prob = synth.preset(a.workload)
     ctx = binding.Context()
     P = ctx.problem(prob)
-    o = binding.opts_from(prob.tol, precision=binding.MIXED if a.precision == "mixed" else binding.FP64)
+    over = dict(precision=binding.MIXED if a.precision == "mixed" else binding.FP64,
+                rounding=binding.ROUND_RANDOMIZED if a.rounding == "randomized" else binding.ROUND_EXACT)
+    if a.maxit_picard > 0:
+        over["maxit_picard"] = a.maxit_picard
+    o = binding.opts_from(prob.tol, **over)
+    stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
     l0 = ctx.launches
     for k in range(a.warmup + a.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
-        P.picard(o)
+        e0.record(stream)
+        u, p, st, code = P.picard(o)
+        e1.record(stream)
         torch.cuda.synchronize()
-        print(json.dumps({"solve": k, "s": time.perf_counter() - t0, "launches_before": l0,
-                          "launches": ctx.launches - l0}), flush=True)
+        n = st.picard_its
+        print(json.dumps({"solve": k, "s": time.perf_counter() - t0, "s_events": e0.elapsed_time(e1) / 1000.0,
+                          "launches_before": l0, "launches": ctx.launches - l0, "workload": a.workload,
+                          "precision": a.precision, "rounding": a.rounding, "status": int(code), "picard_its": n,
+                          "stokes_its": st.stokes_its, "gmres_its": list(st.gmres_its[1:n + 1]),
+                          "inner_its": list(st.inner_its[:n + 1]), "rel_res": st.res[n] / st.fnorm,
+                          "u_ranks": u.ranks, "p_ranks": p.ranks}), flush=True)
         l0 = ctx.launches
 
 
