@@ -3,8 +3,9 @@
 // matvec or a Krylov sum is often many times the rank that survives, by an orthonormal
 // basis of ell columns; the deterministic T_eps then runs on the small train.  The
 // energy the sketch misses is estimated with independent Gaussian probes and the
-// sketch widens (ell doubles) until that estimate is a small part of the truncation
-// budget, so ||T(z) - z|| <= eps ||z|| holds with high probability; the deterministic
+// sketch widens (ell doubles) until ten times that estimate is at most a tenth of the
+// truncation budget; the small train is truncated with the rest of the budget, so
+// ||T(z) - z|| <= eps ||z|| holds with high probability; the deterministic
 // route is used when the sketch would not be narrower than R2.  Randomized low-rank
 // approximation with a posteriori probe estimates in the sense of Halko, Martinsson and
 // Tropp (SIAM Review 2011); for TT rounding cf. Al Daas, Ballard et al. (SISC 2023).
@@ -152,8 +153,9 @@ TTPtr round_rand(tt_ctx* c, const tt_t* z, double eps, uint64_t seed, RoundOut* 
         e2 /= q;
         const double nt2 = dot_host(c, xt.get(), xt.get());
         if (!(nt2 == nt2) || std::isinf(nt2) || !(e2 == e2)) TT_THROW(TT_ENAN, "non-finite norm in truncation");
-        // accept when ten times the estimated missed energy is at most 1% of the budget
-        if (10.0 * e2 <= 1e-2 * eps * eps * (nt2 + e2) || nt2 == 0.0) {
+        // accept when ten times the estimated missed energy is at most 10% of the budget;
+        // the small train is then truncated with what remains (at least 90%)
+        if (10.0 * e2 <= 0.1 * eps * eps * (nt2 + e2) || nt2 == 0.0) {
             const double tot2 = nt2 + e2;
             const double eps2 = std::max(eps * eps * tot2 - 10.0 * e2, 0.5 * eps * eps * tot2) / std::max(nt2, 1e-300);
             RoundOut ri;
