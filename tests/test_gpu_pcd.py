@@ -46,11 +46,12 @@ def test_pressure_matrices_match(ctx, small):
         assert abs(got - ref).max() <= 1e-13 * abs(ref).max()
 
 
-def test_pcd_preconditioner_matches(ctx, small):
+def test_pcd_preconditioner_matches(ctx):
     """PCD Schur part to rounding; the inner solve, identical to the LSC one, to its
-    tight inner tolerance."""
+    tight inner tolerance (tiny problem: the oracle's inner solve at 1e-9 is slow)."""
     from paper_1906_06785_gb300 import binding
-    prob, d = small
+    prob = synth.preset("tiny")
+    d = Discretisation(prob)
     P = ctx.problem(prob)
     u = otm.TT(*synth.random_tt(d.n_t, d.n_xi, d.n_u, 2, 3, seed=181))
     p = otm.TT(*synth.random_tt(d.n_t, d.n_xi, d.n_p, 2, 2, seed=182))
