@@ -1224,8 +1224,9 @@ __global__ void k_permute_normalise(int m, int n, const double* __restrict__ W, 
 // spread over up to 16 SMs) for up to kJacobiRingMaxEntries entries; else the one-CTA
 // shared-memory kernel for tiny matrices (or when no cluster can be formed); else the
 // grid kernel with the columns in global memory.  GB300 issues a warp's FP64
-// instruction over 16 cycles of an SM's FP64 pipe, so rounds are bound by FP64
-// instructions per SM: spreading pairs over SMs beats keeping them on one.
+// instruction over 16 cycles of an SM's FP64 pipe and a round is a chain of dependent
+// instructions, so a round is bound by the longer of one warp's chain and the SM's FP64
+// pipe: pairs are spread over as many SMs as a cluster has, a few warps to an SM.
 constexpr long long kJacobiCtaMaxEntries = 4096;
 constexpr long long kJacobiRingMaxEntries = 96 * 1024;
 
