@@ -152,3 +152,16 @@ def test_a_sign_error_in_the_time_coupling_slows_gmres():
     good = _gmres_its(_pcd_preconditioned(d, w))
     bad = _gmres_its(_pcd_preconditioned(d, w, flip_cp=True))
     assert bad >= good + 8
+
+
+def test_pcd_needs_more_gmres_iterations_than_lsc():
+    """Fig. 5.4: with the PCD approximation the Picard steps need more GMRES iterations
+    than with LSC (tiny problem at tight truncation tolerances)."""
+    from oracle.solver import picard
+    prob = synth.preset("tiny")
+    prob.tol.eps_gmres, prob.tol.eps_soln, prob.tol.eps_conv = 1e-8, 1e-10, 1e-8
+    d = Discretisation(prob)
+    _, _, lsc = picard(d, schur="lsc")
+    _, _, pcd = picard(d, schur="pcd")
+    assert sum(pcd["gmres_its"]) > sum(lsc["gmres_its"])
+    assert pcd["picard_its"] >= lsc["picard_its"]
