@@ -14,6 +14,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include <cooperative_groups.h>
 
@@ -1255,8 +1258,26 @@ static void jacobi_grid(tt_ctx* c, int m, int mr, int n, T* W, int ldw, T tol, d
             RingKernel kern = nullptr;
             int G = 0, S = 0, L = 0, threads = 0;
             size_t smem = 0;
+            // the choice depends only on (device, m, n): cached, so that repeated shapes
+            // skip the search and its attribute and occupancy queries
+            struct RingCfg { int v, G, S, L, threads; size_t smem; };
+            static std::mutex cache_mu;
+            static std::map<std::tuple<int, int, int>, RingCfg> cache;
+            const auto key = std::make_tuple(c->device, m, n);
+            bool cached = false;
+            {
+                std::lock_guard<std::mutex> lk(cache_mu);
+                const auto it = cache.find(key);
+                if (it != cache.end()) {
+                    const RingCfg& r = it->second;
+                    kern = r.v >= 0 ? kerns[r.v] : nullptr;
+                    G = r.G; S = r.S; L = r.L; threads = r.threads; smem = r.smem;
+                    cached = true;
+                }
+            }
             double best = 1e30;
-            for (int v = 0; v < 5; ++v) {
+            int vbest = -1;
+            for (int v = 0; v < 5 && !cached; ++v) {
                 for (int l : {4, 8, 16, 32}) {
                     if (l * kvs[v] < m || (kvs[v] > 2 && l * kvs[v] >= 2 * m)) continue;
                     int lg = 0;
@@ -1278,6 +1299,7 @@ static void jacobi_grid(tt_ctx* c, int m, int mr, int n, T* W, int ldw, T tol, d
                         if (max_cluster_ctas(c, (const void*)kerns[v], 32 * warps, sm) < gg) continue;
                         best = cost;
                         kern = kerns[v];
+                        vbest = v;
                         G = gg;
                         S = s;
                         L = l;
@@ -1286,7 +1308,11 @@ static void jacobi_grid(tt_ctx* c, int m, int mr, int n, T* W, int ldw, T tol, d
                     }
                 }
             }
-            if (G >= 2) {
+            if (!cached) {
+                std::lock_guard<std::mutex> lk(cache_mu);
+                cache[key] = RingCfg{G >= 2 ? vbest : -1, G, S, L, threads, smem};
+            }
+            if (G >= 2 && kern) {
                 DBuf<int> flags(c, max_sweeps + 1);
                 CUDA_CHECK(cudaMemsetAsync(flags.p, 0, (max_sweeps + 1) * sizeof(int), c->stream));
                 int* sweeps = flags.p + max_sweeps;
